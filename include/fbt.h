@@ -1,0 +1,185 @@
+/*
+ * fbt.h - C ABI of the GB300 Fisher-BT library (libfbt.so).
+ *
+ * Exact Gaussian log-likelihood, score and expected Fisher information of a zero-mean Matern
+ * random field, and the Fisher-BT maximiser built on them (Hong, Abdulah, Genton & Sun,
+ * "Fisher Scoring for Exact Matern Covariance Estimation through Stable Smoothness
+ * Optimization", arXiv 2601.11437).
+ *
+ * Model (Sec. 2.1): theta = (sigma^2, alpha, nu), all > 0;
+ *   C(h; theta) = sigma^2 / (2^(nu-1) Gamma(nu)) (h/alpha)^nu K_nu(h/alpha),
+ *   Sigma_ij = C(||s_i - s_j||; theta), plus a diagonal jitter delta (the paper has none):
+ *   Sigma = sigma^2 (R + delta I), R the Matern correlation, so that d Sigma / d sigma^2 =
+ *   Sigma / sigma^2 exactly (the premise of Algorithm 3, Step 2).
+ *   l(theta) = -n/2 log(2 pi) - 1/2 log det Sigma - 1/2 z^T Sigma^-1 z               (Eq. 1)
+ *   l_i      = -1/2 tr(Sigma^-1 Sigma_i) + 1/2 z^T Sigma^-1 Sigma_i Sigma^-1 z          (Eq. 2)
+ *   I_ij     =  1/2 tr(Sigma^-1 Sigma_i Sigma^-1 Sigma_j)                              (Eq. 3)
+ *
+ * Conventions
+ *   - Every entry point returns an fbt_status (0 = success); fbt_strerror() names it.
+ *   - All floating point is IEEE binary64.  Arrays passed in are read, never retained: the
+ *     context copies what it needs.  Outputs are caller-allocated host arrays.
+ *   - Pointers marked "host or device" are host pointers unless the matching *_on_device flag
+ *     is non-zero, in which case they are device pointers on the context's device.
+ *   - A context is not thread safe; use one context per host thread.  All device work of a
+ *     context runs on the CUDA stream given at creation (NULL = legacy default stream), and
+ *     every entry point that returns numbers synchronises that stream before returning.
+ *   - The device work of every evaluation runs in this library's CUDA kernels (sm_103a).  No
+ *     CPU fallback exists: without a usable GPU, fbt_create returns FBT_ERR_CUDA.
+ */
+#ifndef FBT_H
+#define FBT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FBT_OK = 0,
+    FBT_ERR_DOMAIN = 1,   /* a theta_i <= 0 or non-finite: l is -inf, nothing is computed      */
+    FBT_ERR_NOT_PD = 2,   /* a Cholesky pivot was <= 0 or not finite: loglik = -inf, the score */
+                          /* and Fisher outputs are left untouched                             */
+    FBT_ERR_BESSEL = 3,   /* a generated covariance entry was not finite                        */
+    FBT_ERR_TIMEOUT = 4,  /* a bounded device wait expired                                      */
+    FBT_ERR_CUDA = 5,     /* a CUDA runtime call failed (message: fbt_last_cuda_error)          */
+    FBT_ERR_OOM = 6,      /* device memory could not be obtained or the workspace is too small */
+    FBT_ERR_ARG = 7,      /* invalid argument (NULL pointer, n < 1, unsupported option)         */
+    FBT_ERR_STATE = 8     /* fisher_bt_step on a state that is not running                      */
+} fbt_status;
+
+/* Options of a context.  fbt_default_opts() fills the defaults. */
+typedef struct {
+    double jitter;        /* delta of Sigma = sigma^2 (R + delta I); default 1e-8                 */
+    int nb;               /* tile size: 64 or 128 (0 = default 128)                                */
+    int reorder;          /* 1 (default): Z-order (Morton) reordering of the locations; results  */
+                          /* are permutation invariant, the reordering groups near locations     */
+    int with_derivatives; /* 1 (default): workspace for mle_eval; 0: mle_loglik only             */
+    int device;           /* CUDA device ordinal; default 0                                        */
+} fbt_opts;
+
+void fbt_default_opts(fbt_opts* opts);
+
+typedef struct fbt_ctx fbt_ctx;   /* opaque: owns the device copies of locations and field,  */
+                                  /* the tile workspace and the per-evaluation scratch        */
+
+/* Device bytes the workspace of a context for n locations needs (0 on invalid input). */
+size_t fbt_workspace_bytes(long long n, const fbt_opts* opts);
+
+/*
+ * Create a context for n locations and one observed field.
+ *   locs      n x 2 row-major (x_i, y_i), host or device (locs_on_device)
+ *   z         n values, host or device (z_on_device)
+ *   workspace device memory of at least fbt_workspace_bytes(n, opts) bytes, 256-byte aligned,
+ *             owned by the caller and kept alive until fbt_destroy; NULL = the library
+ *             allocates (and frees) it itself with cudaMalloc
+ *   stream    a cudaStream_t on opts->device, or NULL
+ * Locations and field are copied to the device, reordered (Sec. "a0" of the design: Z-order)
+ * and padded to whole tiles.  On failure *out is NULL.
+ */
+fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device,
+                      const double* z, int z_on_device, long long n,
+                      const fbt_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream);
+
+/* Replace the observed field (n values, host or device); locations and workspace are kept. */
+fbt_status fbt_set_field(fbt_ctx* ctx, const double* z, int z_on_device);
+
+/*
+ * Algorithm 2 (Sec. 2.2): l(theta) for theta = (sigma^2, alpha, nu).
+ * Covariance generation, tiled Cholesky, log-determinant 2 sum log L_ii, Y = L^-1 z, Y^T Y.
+ * FBT_ERR_DOMAIN / FBT_ERR_NOT_PD set *loglik = -inf.
+ */
+fbt_status mle_loglik(fbt_ctx* ctx, const double theta[3], double* loglik);
+
+/*
+ * Algorithm 3 (Sec. 2.2): l(theta), score[3] = grad l (Eq. 2), fisher[9] = I(theta) (Eq. 3,
+ * row-major, symmetric).  Requires with_derivatives.  Sigma_alpha and Sigma_nu come from the
+ * partials of the Matern function (Sec. 2.2 and Supp. A); tr(Sigma^-1 Sigma_i Sigma^-1 Sigma_j)
+ * is evaluated as the Frobenius product <B_i, B_j> of B_i = L^-1 Sigma_i L^-T, which equals
+ * the trace of Eq. 3 (the role Eq. 4 plays in the paper).
+ */
+fbt_status mle_eval(fbt_ctx* ctx, const double theta[3], double* loglik,
+                    double score[3], double fisher[9]);
+
+/* Options of the Fisher-BT driver (Algorithm 1, Sec. 2.1); fbt_default_bt_opts() fills the
+ * paper's values: armijo_c 0.001, rho 0.5, slack 0.001, grad_tol 0.001, max_ll_calls 60,
+ * max_grad_calls 20, nm_ftol 1e-9 (plus nm_max_calls 1000, max_halvings 64 as guards). */
+typedef struct {
+    double armijo_c, rho, slack, grad_tol, nm_ftol;
+    int max_ll_calls, max_grad_calls, nm_max_calls, max_halvings;
+} fbt_bt_opts;
+
+void fbt_default_bt_opts(fbt_bt_opts* opts);
+
+enum { FBT_RUNNING = 0, FBT_CONVERGED = 1, FBT_SHIFT = 2, FBT_DONE_NM = 3, FBT_FAILED = -1 };
+
+/* State of a Fisher-BT run (Algorithm 1): theta^(t), phi^(t) = I^-1 grad l, l, grad l, I at
+ * theta^(t), the call counters of the shift rule, the accepted-step count and the state. */
+typedef struct {
+    double theta[3], phi[3], loglik, score[3], fisher[9];
+    int n_ll, n_grad, iter, state, halvings;
+} fbt_state;
+
+/*
+ * Start Algorithm 1: theta0 given (non-NULL), else the best of the nine L9 candidates of
+ * Table 1 built from theta_lo and theta_hi; then one Fisher scoring iteration.
+ */
+fbt_status fisher_bt_start(fbt_ctx* ctx, const double* theta0, const double* theta_lo,
+                           const double* theta_hi, const fbt_bt_opts* bt, fbt_state* st);
+
+/*
+ * One accepted Fisher-BT step (Algorithm 1's loop body): halve phi until the relaxed Armijo
+ * condition (Eq. 5 with c = 0.001 and slack 0.001) holds, evaluating mle_loglik on the host's
+ * behalf for each candidate; theta <- theta + phi; one Fisher scoring iteration (mle_eval).
+ * Sets st->state to FBT_CONVERGED (||grad l||_2 <= grad_tol) or FBT_SHIFT (call limits exceeded
+ * or I not positive definite).  FBT_ERR_STATE if st->state != FBT_RUNNING.
+ */
+fbt_status fisher_bt_step(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts* bt);
+
+/* Algorithm 1 end to end, including the Nelder-Mead fallback and its final Fisher evaluation. */
+fbt_status fisher_bt_run(fbt_ctx* ctx, const double* theta0, const double* theta_lo,
+                         const double* theta_hi, const fbt_bt_opts* bt, fbt_state* out);
+
+/* Per-kernel statistics, recorded with CUDA events on the context's stream while enabled. */
+typedef struct {
+    const char* name;     /* kernel family                                                    */
+    long long launches;   /* launches recorded                                                */
+    double ms;            /* summed device time of those launches                             */
+    double flops;         /* algorithmic floating-point operations of those launches          */
+    double bytes;         /* algorithmic DRAM bytes of those launches                         */
+} fbt_kernel_stat;
+
+/* Enable (1) or disable (0) per-kernel event timing; enabling clears the counters. */
+fbt_status fbt_profile(fbt_ctx* ctx, int enable);
+/* Copy up to cap entries of the statistics into out; *count receives the number of families. */
+fbt_status fbt_profile_read(fbt_ctx* ctx, fbt_kernel_stat* out, int cap, int* count);
+/* Number of this library's kernel launches since creation (or the last reset). */
+long long fbt_launch_count(fbt_ctx* ctx, int reset);
+
+/* Bytes this context has copied host-to-device and device-to-host since creation (or the last
+ * reset), inputs and results included; either pointer may be NULL. */
+fbt_status fbt_transfer_bytes(fbt_ctx* ctx, long long* h2d, long long* d2h, int reset);
+
+/* Geometry of a context: padded size, tile size, tile count per side. */
+fbt_status fbt_geometry(fbt_ctx* ctx, long long* n, long long* n_pad, int* nb, int* tiles);
+
+/* Copy the lower-tile slab (which = 0: Sigma or its Cholesky factor, 1: Sigma_alpha or B_alpha,
+ * 2: Sigma_nu or B_nu, whichever the last call left there) to a host or device buffer of
+ * tiles*(tiles+1)/2 * nb*nb doubles (fbt_geometry).  Tile (i, j), i >= j, starts at
+ * (j*tiles - j*(j-1)/2 + i - j) * nb*nb and is column-major inside.  Test hook. */
+fbt_status fbt_copy_slab(fbt_ctx* ctx, int which, double* dst, int dst_on_device);
+/* Permutation applied to the locations: perm[i] = caller index of reordered point i. */
+fbt_status fbt_copy_perm(fbt_ctx* ctx, long long* perm);
+/* Generate Sigma, Sigma_alpha, Sigma_nu at theta into the slabs without factorising (test hook). */
+fbt_status fbt_generate(fbt_ctx* ctx, const double theta[3], int with_derivatives);
+
+void fbt_destroy(fbt_ctx* ctx);
+const char* fbt_strerror(int status);
+const char* fbt_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBT_H */

@@ -1,0 +1,469 @@
+// C ABI of libfbt: context management, the evaluation pipelines of Algorithm 2 (mle_loglik)
+// and Algorithm 3 (mle_eval), per-kernel profiling and test hooks.  See include/fbt.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fbt.h"
+#include "fbt_kernels.cuh"
+
+using namespace fbt;
+
+// ------------------------------------------------------------------------------------------
+// profiling
+// ------------------------------------------------------------------------------------------
+namespace fbt {
+
+struct FamilyStat {
+    std::string name;
+    long long groups = 0, launches = 0;
+    double ms = 0.0, flops = 0.0, bytes = 0.0;
+};
+struct Pending {
+    int fam;
+    cudaEvent_t a, b;
+    double flops, bytes;
+    int launches;
+};
+struct Profiler {
+    std::vector<FamilyStat> fams;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    int family_id(const char* name) {
+        for (size_t i = 0; i < fams.size(); ++i)
+            if (fams[i].name == name) return (int)i;
+        fams.push_back(FamilyStat{name});
+        return (int)fams.size() - 1;
+    }
+    cudaEvent_t get_event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void flush() {
+        for (auto& p : pending) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p.a, p.b);
+            auto& f = fams[p.fam];
+            f.groups += 1;
+            f.launches += p.launches;
+            f.ms += ms;
+            f.flops += p.flops;
+            f.bytes += p.bytes;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    ~Profiler() {
+        for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+static thread_local cudaEvent_t tl_start;
+
+void Launcher::begin(const char* family_name) {
+    launches_in_group = 0;
+    if (prof) {
+        family = prof->family_id(family_name);
+        tl_start = prof->get_event();
+        cudaEventRecord(tl_start, stream);
+    }
+}
+
+int Launcher::end(double flops, double bytes) {
+    cudaError_t e = cudaGetLastError();
+    if (prof) {
+        cudaEvent_t stop = prof->get_event();
+        cudaEventRecord(stop, stream);
+        prof->pending.push_back(Pending{family, tl_start, stop, flops, bytes, launches_in_group});
+    }
+    return (int)e;
+}
+
+}  // namespace fbt
+
+// ------------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------------
+struct fbt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    fbt_opts opts;
+    Geom g;
+    int nstrips = 0;
+    bool own_ws = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    double *X = nullptr, *Y = nullptr, *Z = nullptr, *vy = nullptr, *vw = nullptr, *bbox = nullptr;
+    long long* perm = nullptr;
+    ThetaConsts* tc = nullptr;
+    QuadTables* qt = nullptr;
+    Slots slots{};
+    int* status = nullptr;
+    EvalOut* out = nullptr;
+    double *S = nullptr, *SA = nullptr, *SN = nullptr;
+    Profiler* prof = nullptr;
+    long long launches = 0;
+    long long h2d_bytes = 0, d2h_bytes = 0;
+    EvalOut host_out{};
+};
+
+static thread_local std::string tl_cuda_error;
+
+static fbt_status cuda_fail(cudaError_t e, const char* where) {
+    tl_cuda_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return FBT_ERR_CUDA;
+}
+#define CK(call, where)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);          \
+    } while (0)
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Computes the workspace layout; when base is non-null, also assigns the context's pointers.
+static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
+    const int nb = o.nb;
+    const long long T = (n + nb - 1) / nb;
+    const long long npad = T * nb;
+    const long long tiles = T * (T + 1) / 2;
+    const int ns = nb / 32;
+    const size_t slab = (size_t)tiles * nb * nb * sizeof(double);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align256(off + bytes);
+        return base ? base + at : nullptr;
+    };
+    char* pX = take(npad * 8);
+    char* pY = take(npad * 8);
+    char* pZ = take(npad * 8);
+    char* pvy = take(npad * 8);
+    char* pvw = take(npad * 8);
+    char* pperm = take((size_t)n * 8);
+    char* pbbox = take(4 * 8);
+    char* ptc = take(sizeof(ThetaConsts));
+    char* pqt = take(sizeof(QuadTables));
+    char* pld = take((size_t)T * 8);
+    char* pqf = take((size_t)tiles * 2 * 8);
+    char* pdg = take((size_t)T * ns * 5 * 8);
+    char* pod = take((size_t)tiles * ns * 3 * 8);
+    char* pst = take(sizeof(int) * 4);
+    char* pout = take(sizeof(EvalOut));
+    char* pS = take(slab);
+    char* pSA = o.with_derivatives ? take(slab) : nullptr;
+    char* pSN = o.with_derivatives ? take(slab) : nullptr;
+    if (base && c) {
+        c->X = (double*)pX; c->Y = (double*)pY; c->Z = (double*)pZ;
+        c->vy = (double*)pvy; c->vw = (double*)pvw;
+        c->perm = (long long*)pperm; c->bbox = (double*)pbbox;
+        c->tc = (ThetaConsts*)ptc; c->qt = (QuadTables*)pqt;
+        c->slots.logdet = (double*)pld; c->slots.qform = (double*)pqf;
+        c->slots.diag = (double*)pdg; c->slots.offd = (double*)pod;
+        c->status = (int*)pst; c->out = (EvalOut*)pout;
+        c->S = (double*)pS; c->SA = (double*)pSA; c->SN = (double*)pSN;
+    }
+    return off;
+}
+
+static bool opts_valid(const fbt_opts& o) {
+    return (o.nb == 64 || o.nb == 128) && o.jitter >= 0.0 && isfinite(o.jitter) && o.device >= 0;
+}
+
+extern "C" {
+
+void fbt_default_opts(fbt_opts* o) {
+    if (!o) return;
+    o->jitter = 1e-8;
+    o->nb = 128;
+    o->reorder = 1;
+    o->with_derivatives = 1;
+    o->device = 0;
+}
+
+size_t fbt_workspace_bytes(long long n, const fbt_opts* opts) {
+    fbt_opts o;
+    fbt_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.nb == 0) o.nb = 128;
+    if (n < 1 || !opts_valid(o)) return 0;
+    return carve(n, o, nullptr, nullptr);
+}
+
+static Launcher launcher(fbt_ctx* c) {
+    Launcher L;
+    L.stream = c->stream;
+    L.prof = c->prof;
+    L.launches = &c->launches;
+    return L;
+}
+
+fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device, const double* z,
+                      int z_on_device, long long n, const fbt_opts* opts, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    if (!out) return FBT_ERR_ARG;
+    *out = nullptr;
+    if (!locs || !z || n < 1 || n > (1ll << 31)) return FBT_ERR_ARG;
+    fbt_opts o;
+    fbt_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.nb == 0) o.nb = 128;
+    if (!opts_valid(o)) return FBT_ERR_ARG;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (o.device >= ndev) return FBT_ERR_ARG;
+    CK(cudaSetDevice(o.device), "cudaSetDevice");
+    const size_t need = carve(n, o, nullptr, nullptr);
+    fbt_ctx* c = new fbt_ctx();
+    c->device = o.device;
+    c->stream = (cudaStream_t)stream;
+    c->opts = o;
+    c->g.n = n;
+    c->g.nb = o.nb;
+    c->g.T = (int)((n + o.nb - 1) / o.nb);
+    c->g.npad = (long long)c->g.T * o.nb;
+    c->nstrips = strips_per_tile(o.nb);
+    if (workspace) {
+        if (workspace_bytes < need || ((uintptr_t)workspace & 255)) { delete c; return FBT_ERR_OOM; }
+        c->ws = (char*)workspace;
+        c->ws_bytes = workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&c->ws, need);
+        if (e != cudaSuccess) { cudaGetLastError(); delete c; return FBT_ERR_OOM; }
+        c->own_ws = true;
+        c->ws_bytes = need;
+    }
+    carve(n, o, c->ws, c);
+    // staging inside the (not yet used) Sigma slab: sort keys, raw locations, raw field
+    long long npow2 = 1;
+    while (npow2 < n) npow2 <<= 1;
+    unsigned long long* keys = (unsigned long long*)c->S;
+    double* raw_locs = (double*)(keys + npow2);
+    double* raw_z = raw_locs + 2 * n;
+    fbt_status st = FBT_OK;
+    do {
+        cudaError_t e;
+        e = cudaMemcpyAsync(raw_locs, locs, (size_t)n * 2 * sizeof(double),
+                            locs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "copy locations"); break; }
+        e = cudaMemcpyAsync(raw_z, z, (size_t)n * sizeof(double),
+                            z_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "copy field"); break; }
+        c->h2d_bytes += (locs_on_device ? 0 : 16ll * n) + (z_on_device ? 0 : 8ll * n);
+        Launcher L = launcher(c);
+        int rc = launch_reorder(L, raw_locs, raw_z, n, c->g.npad, o.reorder, keys, c->bbox, c->X,
+                                c->Y, c->Z, c->perm);
+        if (rc) { st = cuda_fail((cudaError_t)rc, "reorder"); break; }
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "reorder sync"); break; }
+    } while (0);
+    if (st != FBT_OK) { fbt_destroy(c); return st; }
+    *out = c;
+    return FBT_OK;
+}
+
+fbt_status fbt_set_field(fbt_ctx* c, const double* z, int z_on_device) {
+    if (!c || !z) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    double* raw_z = c->vw;    // staging: the w vector is rebuilt by every evaluation
+    CK(cudaMemcpyAsync(raw_z, z, (size_t)c->g.n * sizeof(double),
+                       z_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+       "copy field");
+    if (!z_on_device) c->h2d_bytes += 8ll * c->g.n;
+    Launcher L = launcher(c);
+    int rc = launch_permute_field(L, raw_z, c->perm, c->g.n, c->g.npad, c->Z);
+    if (rc) return cuda_fail((cudaError_t)rc, "permute field");
+    CK(cudaStreamSynchronize(c->stream), "set_field sync");
+    return FBT_OK;
+}
+
+static bool theta_ok(const double* th) {
+    return th && isfinite(th[0]) && isfinite(th[1]) && isfinite(th[2]) && th[0] > 0 && th[1] > 0 &&
+           th[2] > 0;
+}
+
+// Shared pipeline of Algorithms 2 and 3.
+static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    Launcher L = launcher(c);
+    const Geom& g = c->g;
+    int rc = 0;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
+    if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
+    if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN, deriv, c->status)))
+        return cuda_fail((cudaError_t)rc, "generate");
+    if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status))) return cuda_fail((cudaError_t)rc, "potrf");
+    CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if (deriv) {
+        CK(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+        if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
+        if ((rc = launch_qform(L, g, c->SA, c->SN, c->vw, c->slots.qform))) return cuda_fail((cudaError_t)rc, "qform");
+        // the off-diagonal product slots are indexed by tile; those of diagonal tiles are never
+        // written by the transform and must read as zero in the assembly
+        CK(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
+           "clear slots");
+        if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd)))
+            return cuda_fail((cudaError_t)rc, "sygst");
+    }
+    if ((rc = launch_assemble(L, g, c->vy, c->slots, deriv, c->tc, c->status, c->out)))
+        return cuda_fail((cudaError_t)rc, "assemble");
+    CK(cudaMemcpyAsync(&c->host_out, c->out, sizeof(EvalOut), cudaMemcpyDeviceToHost, c->stream), "copy result");
+    c->d2h_bytes += (long long)sizeof(EvalOut);
+    CK(cudaStreamSynchronize(c->stream), "evaluation sync");
+    if (c->prof) c->prof->flush();
+    if (c->host_out.status & ST_NOT_PD) return FBT_ERR_NOT_PD;
+    if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
+    return FBT_OK;
+}
+
+fbt_status mle_loglik(fbt_ctx* c, const double theta[3], double* loglik) {
+    if (!c || !theta || !loglik) return FBT_ERR_ARG;
+    if (!theta_ok(theta)) { *loglik = -INFINITY; return FBT_ERR_DOMAIN; }
+    fbt_status st = evaluate(c, theta, false);
+    *loglik = st == FBT_OK ? c->host_out.loglik : -INFINITY;
+    return st;
+}
+
+fbt_status mle_eval(fbt_ctx* c, const double theta[3], double* loglik, double score[3],
+                    double fisher[9]) {
+    if (!c || !theta || !loglik || !score || !fisher) return FBT_ERR_ARG;
+    if (!c->opts.with_derivatives) return FBT_ERR_ARG;
+    if (!theta_ok(theta)) { *loglik = -INFINITY; return FBT_ERR_DOMAIN; }
+    fbt_status st = evaluate(c, theta, true);
+    if (st != FBT_OK) { *loglik = -INFINITY; return st; }
+    *loglik = c->host_out.loglik;
+    for (int i = 0; i < 3; ++i) score[i] = c->host_out.score[i];
+    for (int i = 0; i < 9; ++i) fisher[i] = c->host_out.fisher[i];
+    return FBT_OK;
+}
+
+fbt_status fbt_generate(fbt_ctx* c, const double theta[3], int with_derivatives) {
+    if (!c || !theta) return FBT_ERR_ARG;
+    if (with_derivatives && !c->opts.with_derivatives) return FBT_ERR_ARG;
+    if (!theta_ok(theta)) return FBT_ERR_DOMAIN;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    Launcher L = launcher(c);
+    int rc;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
+    if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
+    if ((rc = launch_generate(L, c->g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN,
+                              with_derivatives != 0, c->status)))
+        return cuda_fail((cudaError_t)rc, "generate");
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
+    CK(cudaStreamSynchronize(c->stream), "generate sync");
+    if (c->prof) c->prof->flush();
+    return (hs & ST_BESSEL) ? FBT_ERR_BESSEL : FBT_OK;
+}
+
+fbt_status fbt_geometry(fbt_ctx* c, long long* n, long long* npad, int* nb, int* tiles) {
+    if (!c) return FBT_ERR_ARG;
+    if (n) *n = c->g.n;
+    if (npad) *npad = c->g.npad;
+    if (nb) *nb = c->g.nb;
+    if (tiles) *tiles = c->g.T;
+    return FBT_OK;
+}
+
+fbt_status fbt_copy_slab(fbt_ctx* c, int which, double* dst, int dst_on_device) {
+    if (!c || !dst || which < 0 || which > 2) return FBT_ERR_ARG;
+    const double* src = which == 0 ? c->S : which == 1 ? c->SA : c->SN;
+    if (!src) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t bytes = (size_t)num_tiles(c->g.T) * c->g.nb * c->g.nb * sizeof(double);
+    CK(cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream), "copy slab");
+    CK(cudaStreamSynchronize(c->stream), "copy slab sync");
+    return FBT_OK;
+}
+
+fbt_status fbt_copy_perm(fbt_ctx* c, long long* perm) {
+    if (!c || !perm) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaMemcpyAsync(perm, c->perm, (size_t)c->g.n * sizeof(long long), cudaMemcpyDeviceToHost, c->stream),
+       "copy perm");
+    CK(cudaStreamSynchronize(c->stream), "copy perm sync");
+    return FBT_OK;
+}
+
+fbt_status fbt_profile(fbt_ctx* c, int enable) {
+    if (!c) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->stream), "profile sync");
+    delete c->prof;
+    c->prof = enable ? new Profiler() : nullptr;
+    return FBT_OK;
+}
+
+fbt_status fbt_profile_read(fbt_ctx* c, fbt_kernel_stat* out, int cap, int* count) {
+    if (!c || !count) return FBT_ERR_ARG;
+    if (!c->prof) { *count = 0; return FBT_OK; }
+    CK(cudaStreamSynchronize(c->stream), "profile sync");
+    c->prof->flush();
+    const int nf = (int)c->prof->fams.size();
+    *count = nf;
+    for (int i = 0; i < nf && i < cap && out; ++i) {
+        const FamilyStat& f = c->prof->fams[i];
+        out[i].name = f.name.c_str();
+        out[i].launches = f.groups;
+        out[i].ms = f.ms;
+        out[i].flops = f.flops;
+        out[i].bytes = f.bytes;
+    }
+    return FBT_OK;
+}
+
+fbt_status fbt_transfer_bytes(fbt_ctx* c, long long* h2d, long long* d2h, int reset) {
+    if (!c) return FBT_ERR_ARG;
+    if (h2d) *h2d = c->h2d_bytes;
+    if (d2h) *d2h = c->d2h_bytes;
+    if (reset) c->h2d_bytes = c->d2h_bytes = 0;
+    return FBT_OK;
+}
+
+long long fbt_launch_count(fbt_ctx* c, int reset) {
+    if (!c) return -1;
+    long long v = c->launches;
+    if (reset) c->launches = 0;
+    return v;
+}
+
+void fbt_destroy(fbt_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c->prof;
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+}
+
+const char* fbt_strerror(int s) {
+    switch (s) {
+        case FBT_OK: return "ok";
+        case FBT_ERR_DOMAIN: return "parameter outside the domain (theta_i <= 0 or not finite)";
+        case FBT_ERR_NOT_PD: return "covariance matrix not positive definite (Cholesky pivot <= 0)";
+        case FBT_ERR_BESSEL: return "non-finite covariance entry";
+        case FBT_ERR_TIMEOUT: return "bounded device wait expired";
+        case FBT_ERR_CUDA: return "CUDA runtime error";
+        case FBT_ERR_OOM: return "device memory unavailable or workspace too small";
+        case FBT_ERR_ARG: return "invalid argument";
+        case FBT_ERR_STATE: return "Fisher-BT state is not running";
+        default: return "unknown status";
+    }
+}
+
+const char* fbt_last_cuda_error(void) { return tl_cuda_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,421 @@
+// Steps a2, a3, a7, a8: tiled FP64 Cholesky with log-det partials, and the two-sided transform
+// B_i = L^-1 Sigma_i L^-T of both derivative matrices with fused trace / Frobenius partials.
+//
+// On GB300 the FP64 rate is set by the DFMA pipe (measured 1.19 TFLOP/s over 152 SMs, i.e. two
+// FP64 FMAs per clock per SM; the FP64 mma.sync path measured 1.05 TFLOP/s), so these kernels
+// are plain DFMA register-blocked tiles: every SM must simply be kept issuing DFMAs.
+//
+// Cholesky (Algorithm 2/3 step "Cholesky factorization"), right-looking over tile steps k:
+//   L_kk = chol(S_kk); L_ik = S_ik L_kk^-T (i > k); S_ij -= L_ik L_jk^T (k < j <= i).
+// Two-sided transform (replaces the paper's A_i = Sigma^-1 Sigma_i, whose traces Eq. 3 needs:
+// tr(Sigma^-1 S_a Sigma^-1 S_b) = <B_a, B_b>_F and tr(Sigma^-1 S_a) = tr B_a), by the tile
+// recursion of the blocked LAPACK-style algorithm, step k:
+//   B_kk = L_kk^-1 M_kk L_kk^-T
+//   C_ik = M_ik L_kk^-T,  E_ik = C_ik - 1/2 L_ik B_kk                       (i > k)
+//   M_ij -= L_ik E_jk^T + E_ik L_jk^T                                       (k < j <= i)
+//   P_ik = E_ik - 1/2 L_ik B_kk
+// and finally B_(k+1:,k) = L_(k+1:,k+1:)^-1 P_(k+1:,k), done for all columns at once as a
+// left-looking tile forward substitution over rows m (TRSM with L_mm, then GEMM updates).
+#include <math.h>
+
+#include "fbt_kernels.cuh"
+
+namespace fbt {
+
+// ------------------------------------------------------------------------------------------
+// Diagonal tile Cholesky (one CTA, tile resident in shared memory)
+// ------------------------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int T, int k,
+                                                    double* __restrict__ logdet_slots,
+                                                    int* status) {
+    extern __shared__ double A[];
+    constexpr int LD = NB + 1;
+    __shared__ double s_inv;
+    __shared__ int s_bad;
+    double* tile = S + tile_offset(k, k, T, NB);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        A[r + c * LD] = r >= c ? tile[e] : 0.0;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < NB; ++j) {
+        if (threadIdx.x == 0) {
+            double d = A[j + j * LD];
+            if (!(d > 0.0) || !isfinite(d)) { s_bad = 1; d = 1.0; }
+            const double l = sqrt(d);
+            A[j + j * LD] = l;
+            s_inv = 1.0 / l;
+        }
+        __syncthreads();
+        for (int r = j + 1 + threadIdx.x; r < NB; r += blockDim.x) A[r + j * LD] *= s_inv;
+        __syncthreads();
+        const int m = NB - j - 1;
+        for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+            const int rr = q % m, cc = q / m;
+            if (rr >= cc) {
+                const int r = j + 1 + rr, c = j + 1 + cc;
+                A[r + c * LD] -= A[r + j * LD] * A[c + j * LD];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        tile[e] = r >= c ? A[r + c * LD] : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int j = 0; j < NB; ++j) s += log(A[j + j * LD]);
+        logdet_slots[k] = s;
+        if (s_bad) atomicOr(status, ST_NOT_PD);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Strip triangular solves.  A strip is 32 rows (RIGHT: X = A L^-T) or 32 columns (LEFT:
+// X = L^-1 A) of a target tile; each of the 32 strip vectors v obeys the same forward
+// substitution v_d /= L_dd, v_d' -= L_d'd v_d (d' > d).  Up to two target tiles share L.
+// ------------------------------------------------------------------------------------------
+enum TrsmMode : int {
+    TRSM_POTRF_PANEL = 0,   // targets S(i,k), i > k;            RIGHT, 1 matrix
+    TRSM_SYGST_DIAG_R = 1,  // targets M(k,k);                   RIGHT, 2 matrices
+    TRSM_SYGST_DIAG_L = 2,  // targets M(k,k);                   LEFT,  2 matrices, diag epilogue
+    TRSM_SYGST_PANEL = 3,   // targets M(i,k), i > k;            RIGHT, 2 matrices
+    TRSM_SYGST_ROW = 4      // targets M(m,kk), kk < m, L=S(m,m); LEFT, 2 matrices, off-diag epilogue
+};
+
+struct TrsmParams {
+    int mode, k, T;
+    const double* S;
+    double* M0;
+    double* M1;
+    double* slots;
+};
+
+constexpr int STRIP = 32;
+
+int strips_per_tile(int nb) { return nb / STRIP; }
+
+template <int NB, bool LEFT, int NMAT, int EPI>
+__global__ void __launch_bounds__(256) k_trsm_strip(TrsmParams p) {
+    extern __shared__ double V[];                      // [NMAT][STRIP][NB + 1]
+    constexpr int LDV = NB + 1;
+    constexpr int NSTRIPS = NB / STRIP;
+    __shared__ double s_inv[NB];
+    __shared__ double s_red[STRIP][8];
+    const int task = blockIdx.x / NSTRIPS, strip = blockIdx.x % NSTRIPS;
+    const int T = p.T;
+    int li, ti, tj;   // L tile (li, li); target tile (ti, tj)
+    switch (p.mode) {
+        case TRSM_POTRF_PANEL: li = p.k; ti = p.k + 1 + task; tj = p.k; break;
+        case TRSM_SYGST_DIAG_R:
+        case TRSM_SYGST_DIAG_L: li = p.k; ti = p.k; tj = p.k; break;
+        case TRSM_SYGST_PANEL: li = p.k; ti = p.k + 1 + task; tj = p.k; break;
+        default: li = p.k; ti = p.k; tj = task; break;   // TRSM_SYGST_ROW, m = p.k
+    }
+    const double* __restrict__ Lt = p.S + tile_offset(li, li, T, NB);
+    const long long toff = tile_offset(ti, tj, T, NB);
+    double* tgt[2];
+    tgt[0] = (NMAT == 1 ? const_cast<double*>(p.S) : p.M0) + toff;
+    tgt[1] = NMAT == 2 ? p.M1 + toff : nullptr;
+    const int o = strip * STRIP;
+    for (int m = 0; m < NMAT; ++m) {
+        double* src = tgt[m];
+        for (int e = threadIdx.x; e < STRIP * NB; e += blockDim.x) {
+            int lane, d;
+            double val;
+            if (LEFT) { d = e % NB; lane = e / NB; val = src[d + (long long)(o + lane) * NB]; }
+            else { lane = e % STRIP; d = e / STRIP; val = src[(o + lane) + (long long)d * NB]; }
+            V[(m * STRIP + lane) * LDV + d] = val;
+        }
+    }
+    for (int d = threadIdx.x; d < NB; d += blockDim.x) s_inv[d] = 1.0 / Lt[d + (long long)d * NB];
+    __syncthreads();
+    const int lane = threadIdx.x % STRIP, grp = threadIdx.x / STRIP;   // 8 groups of 32
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int d = 0; d < NB; ++d) {
+        const double* __restrict__ Lcol = Lt + (long long)d * NB;
+        double vv[NMAT];
+#pragma unroll
+        for (int m = 0; m < NMAT; ++m) vv[m] = V[(m * STRIP + lane) * LDV + d] * s_inv[d];
+        if (grp == 0) {
+#pragma unroll
+            for (int m = 0; m < NMAT; ++m) {
+                if (LEFT) tgt[m][d + (long long)(o + lane) * NB] = vv[m];
+                else tgt[m][(o + lane) + (long long)d * NB] = vv[m];
+            }
+            if (EPI == 1) {                       // diagonal tile: traces and Frobenius products
+                if (d == o + lane) { acc[0] += vv[0]; acc[1] += vv[NMAT - 1]; }
+                acc[2] += vv[0] * vv[0];
+                acc[3] += vv[0] * vv[NMAT - 1];
+                acc[4] += vv[NMAT - 1] * vv[NMAT - 1];
+            } else if (EPI == 2) {                // off-diagonal tile: Frobenius products
+                acc[2] += vv[0] * vv[0];
+                acc[3] += vv[0] * vv[NMAT - 1];
+                acc[4] += vv[NMAT - 1] * vv[NMAT - 1];
+            }
+        }
+        for (int dp = d + 1 + grp; dp < NB; dp += 8) {
+            const double l = __ldg(Lcol + dp);
+#pragma unroll
+            for (int m = 0; m < NMAT; ++m) V[(m * STRIP + lane) * LDV + dp] -= vv[m] * l;
+        }
+        __syncthreads();
+    }
+    if (EPI != 0 && grp == 0) {
+        // fixed-order reduction over the 32 lanes of warp 0
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            double v = acc[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            acc[q] = v;
+        }
+        if (lane == 0) {
+            if (EPI == 1) {
+                double* out = p.slots + ((long long)p.k * NSTRIPS + strip) * 5;
+                for (int q = 0; q < 5; ++q) out[q] = acc[q];
+            } else {
+                double* out = p.slots + (tile_index(ti, tj, T) * NSTRIPS + strip) * 3;
+                out[0] = acc[2]; out[1] = acc[3]; out[2] = acc[4];
+            }
+        }
+    }
+    (void)s_red;
+}
+
+// ------------------------------------------------------------------------------------------
+// Tile GEMM: one CTA computes a 64 x 64 block of a target tile,
+//   C -= scale * sum_terms op(A) op(B),  NT: C[r][c] -= A[r][p] B[c][p];  NN: A[r][p] B[p][c]
+// 256 threads as 16 x 16, each a 4 x 4 register block (rows tx + 16a, columns ty + 16b).
+// ------------------------------------------------------------------------------------------
+enum GemmMode : int {
+    GEMM_POTRF_UPD = 0,      // S(i,j) -= S(i,k) S(j,k)^T,  k < j <= i, lower 64-blocks of diagonal tiles
+    GEMM_SYGST_UPD = 1,      // M(i,j) -= S(i,k) M(j,k)^T + M(i,k) S(j,k)^T, k < j <= i, full tiles
+    GEMM_SYGST_FIX = 2,      // M(i,k) -= 1/2 S(i,k) M(k,k),  i > k      (M(k,k) symmetric: NT)
+    GEMM_SYGST_ROWUPD = 3    // M(i,kk) -= S(i,m) M(m,kk),   i > m > kk  (NN)
+};
+
+struct GemmParams {
+    int mode, k, T;
+    const double* S;
+    double* M0;
+    double* M1;
+};
+
+constexpr int GB = 64, GK = 32;
+
+template <int NB, bool NN, int NTERMS>
+__global__ void __launch_bounds__(256) k_gemm_tile(GemmParams p) {
+    constexpr int SB = NB / GB;            // 64-blocks per tile side
+    __shared__ double As[GK][GB];
+    __shared__ double Bs[GK][GB + 1];
+    const int T = p.T, k = p.k;
+    const long long bid = blockIdx.x;
+    const int sub = (int)(bid % (SB * SB));
+    const long long task = bid / (SB * SB);
+    const int sr = sub % SB, sc = sub / SB;
+    double* M = blockIdx.y == 0 ? p.M0 : p.M1;
+    int ci, cj;
+    const double *A1, *B1, *A2 = nullptr, *B2 = nullptr;
+    double scale = 1.0;
+    if (p.mode == GEMM_POTRF_UPD || p.mode == GEMM_SYGST_UPD) {
+        int ii, jj;
+        tri_decode(task, ii, jj);
+        ci = k + 1 + ii;
+        cj = k + 1 + jj;
+        if (p.mode == GEMM_POTRF_UPD) {
+            if (ci == cj && sr < sc) return;           // only the lower triangle of S is used
+            M = const_cast<double*>(p.S);
+            A1 = p.S + tile_offset(ci, k, T, NB);
+            B1 = p.S + tile_offset(cj, k, T, NB);
+        } else {
+            A1 = p.S + tile_offset(ci, k, T, NB);
+            B1 = M + tile_offset(cj, k, T, NB);
+            A2 = M + tile_offset(ci, k, T, NB);
+            B2 = p.S + tile_offset(cj, k, T, NB);
+        }
+    } else if (p.mode == GEMM_SYGST_FIX) {
+        ci = k + 1 + (int)task;
+        cj = k;
+        A1 = p.S + tile_offset(ci, k, T, NB);
+        B1 = M + tile_offset(k, k, T, NB);
+        scale = 0.5;
+    } else {   // GEMM_SYGST_ROWUPD, m = k: tasks (ci, cj) with ci in (m, T), cj in [0, m)
+        const int m = k;
+        cj = (int)(task % m);
+        ci = m + 1 + (int)(task / m);
+        A1 = p.S + tile_offset(ci, m, T, NB);
+        B1 = M + tile_offset(m, cj, T, NB);
+    }
+    double* C = M + tile_offset(ci, cj, T, NB);
+    const int r0 = sr * GB, c0 = sc * GB;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll
+    for (int term = 0; term < NTERMS; ++term) {
+        const double* __restrict__ A = term == 0 ? A1 : A2;
+        const double* __restrict__ B = term == 0 ? B1 : B2;
+        for (int k0 = 0; k0 < NB; k0 += GK) {
+            for (int e = threadIdx.x; e < GK * GB; e += 256) {
+                const int rr = e % GB, kk = e / GB;
+                As[kk][rr] = A[(r0 + rr) + (long long)(k0 + kk) * NB];
+            }
+            if (NN) {
+                for (int e = threadIdx.x; e < GK * GB; e += 256) {
+                    const int kk = e % GK, cc = e / GK;
+                    Bs[kk][cc] = B[(k0 + kk) + (long long)(c0 + cc) * NB];
+                }
+            } else {
+                for (int e = threadIdx.x; e < GK * GB; e += 256) {
+                    const int cc = e % GB, kk = e / GB;
+                    Bs[kk][cc] = B[(c0 + cc) + (long long)(k0 + kk) * NB];
+                }
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < GK; ++kk) {
+                double av[4], bv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            double* cp = C + (r0 + tx + 16 * a) + (long long)(c0 + ty + 16 * b) * NB;
+            *cp -= scale * acc[a][b];
+        }
+}
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+template <int NB>
+static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status) {
+    const int T = g.T;
+    const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
+    const size_t smem_trsm1 = (size_t)STRIP * (NB + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_potrf_diag<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_potrf);
+    cudaFuncSetAttribute(k_trsm_strip<NB, false, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_trsm1);
+    constexpr int NS = NB / STRIP;
+    constexpr int SB = NB / GB;
+    const double nb3 = (double)NB * NB * NB;
+    int rc = 0;
+    for (int k = 0; k < T; ++k) {
+        L.begin("potrf_diag");
+        k_potrf_diag<NB><<<1, 512, smem_potrf, L.stream>>>(S, T, k, logdet_slots, status);
+        L.count();
+        if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
+        const int m = T - k - 1;
+        if (m == 0) break;
+        TrsmParams tp{TRSM_POTRF_PANEL, k, T, S, nullptr, nullptr, nullptr};
+        L.begin("trsm_panel");
+        k_trsm_strip<NB, false, 1, 0><<<m * NS, 256, smem_trsm1, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end((double)m * nb3, 16.0 * m * NB * NB))) return rc;
+        GemmParams gp{GEMM_POTRF_UPD, k, T, S, nullptr, nullptr};
+        const long long tasks = (long long)m * (m + 1) / 2;
+        L.begin("gemm_potrf_update");
+        k_gemm_tile<NB, false, 1><<<dim3((unsigned)(tasks * SB * SB), 1), 256, 0, L.stream>>>(gp);
+        L.count();
+        // algorithmic flops: 2 nb^3 per off-diagonal tile, nb^3 + nb^2 for a diagonal (SYRK) tile
+        const double fl = (double)m * (m - 1) / 2 * 2.0 * nb3 + m * (nb3 + (double)NB * NB);
+        if ((rc = L.end(fl, 8.0 * NB * NB * (3.0 * tasks)))) return rc;
+    }
+    return rc;
+}
+
+int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status) {
+    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status);
+    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status);
+    return cudaErrorInvalidValue;
+}
+
+template <int NB>
+static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
+                      double* diag_slots, double* offd_slots) {
+    const int T = g.T;
+    constexpr int NS = NB / STRIP;
+    constexpr int SB = NB / GB;
+    const size_t smem2 = (size_t)2 * STRIP * (NB + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_trsm_strip<NB, false, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    const double nb3 = (double)NB * NB * NB;
+    const double tb = 8.0 * NB * NB;
+    int rc = 0;
+    for (int k = 0; k < T; ++k) {
+        TrsmParams tp{TRSM_SYGST_DIAG_R, k, T, S, M0, M1, diag_slots};
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, false, 2, 0><<<NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        tp.mode = TRSM_SYGST_DIAG_L;
+        k_trsm_strip<NB, true, 2, 1><<<NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(4.0 * nb3, 6.0 * tb))) return rc;
+        const int m = T - k - 1;
+        if (m == 0) break;
+        tp.mode = TRSM_SYGST_PANEL;
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, false, 2, 0><<<m * NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tb))) return rc;
+        GemmParams gp{GEMM_SYGST_FIX, k, T, S, M0, M1};
+        L.begin("gemm_sygst_fix");
+        k_gemm_tile<NB, false, 1><<<dim3((unsigned)(m * SB * SB), 2), 256, 0, L.stream>>>(gp);
+        L.count();
+        if ((rc = L.end(2.0 * m * 2.0 * nb3, 2.0 * m * 4.0 * tb))) return rc;
+        const long long tasks = (long long)m * (m + 1) / 2;
+        gp.mode = GEMM_SYGST_UPD;
+        L.begin("gemm_sygst_update");
+        k_gemm_tile<NB, false, 2><<<dim3((unsigned)(tasks * SB * SB), 2), 256, 0, L.stream>>>(gp);
+        L.count();
+        if ((rc = L.end(2.0 * tasks * 4.0 * nb3, 2.0 * tasks * 5.0 * tb))) return rc;
+        gp.mode = GEMM_SYGST_FIX;
+        L.begin("gemm_sygst_fix");
+        k_gemm_tile<NB, false, 1><<<dim3((unsigned)(m * SB * SB), 2), 256, 0, L.stream>>>(gp);
+        L.count();
+        if ((rc = L.end(2.0 * m * 2.0 * nb3, 2.0 * m * 4.0 * tb))) return rc;
+    }
+    // B_(m, kk) = L_mm^-1 (P_(m,kk) - sum_(kk<p<m) L_mp B_(p,kk)), row by row
+    for (int m = 1; m < T; ++m) {
+        TrsmParams tp{TRSM_SYGST_ROW, m, T, S, M0, M1, offd_slots};
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, true, 2, 2><<<m * NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tb))) return rc;
+        const int below = T - m - 1;
+        if (below == 0) continue;
+        GemmParams gp{GEMM_SYGST_ROWUPD, m, T, S, M0, M1};
+        const long long tasks = (long long)below * m;
+        L.begin("gemm_sygst_rowupd");
+        k_gemm_tile<NB, true, 1><<<dim3((unsigned)(tasks * SB * SB), 2), 256, 0, L.stream>>>(gp);
+        L.count();
+        if ((rc = L.end(2.0 * tasks * 2.0 * nb3, 2.0 * tasks * 4.0 * tb))) return rc;
+    }
+    return rc;
+}
+
+int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
+                 double* diag_slots, double* offd_slots) {
+    if (g.nb == 128) return sygst_impl<128>(L, g, S, M0, M1, diag_slots, offd_slots);
+    if (g.nb == 64) return sygst_impl<64>(L, g, S, M0, M1, diag_slots, offd_slots);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fbt

@@ -1,0 +1,242 @@
+// Steps a4, a5, a9, a10: triangular solves y = L^-1 z and w = L^-T y (Algorithm 2/3), the
+// quadratic forms w^T Sigma_i w (Algorithm 3, Steps 3-4), and the assembly of l, score and
+// Fisher information (Eq. 1-3, Algorithm 3 Step 2's closed forms for sigma^2).
+//
+// All reductions sum per-tile / per-thread partials in a fixed order, so every result is
+// bitwise reproducible from run to run.
+#include <math.h>
+
+#include "fbt_kernels.cuh"
+
+namespace fbt {
+
+// v_m <- L_mm^-1 v_m (trans = false) or L_mm^-T v_m (trans = true), one CTA.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S, int T, int nb,
+                                                   int m, double* __restrict__ v) {
+    extern __shared__ double sv[];
+    const double* __restrict__ Lt = S + tile_offset(m, m, T, nb);
+    double* vm = v + (long long)m * nb;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
+    __syncthreads();
+    if (!TRANS) {
+        for (int d = 0; d < nb; ++d) {
+            const double x = sv[d] / Lt[d + (long long)d * nb];
+            __syncthreads();
+            if (threadIdx.x == 0) sv[d] = x;
+            for (int dp = d + 1 + threadIdx.x; dp < nb; dp += blockDim.x)
+                sv[dp] -= Lt[dp + (long long)d * nb] * x;
+            __syncthreads();
+        }
+    } else {
+        for (int d = nb - 1; d >= 0; --d) {
+            const double x = sv[d] / Lt[d + (long long)d * nb];
+            __syncthreads();
+            if (threadIdx.x == 0) sv[d] = x;
+            const double* __restrict__ Lrow = Lt + d;     // L[d][dp] = Lt[d + dp * nb], dp < d
+            for (int dp = threadIdx.x; dp < d; dp += blockDim.x) sv[dp] -= Lrow[(long long)dp * nb] * x;
+            __syncthreads();
+        }
+    }
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) vm[d] = sv[d];
+}
+
+// forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i, thread per row)
+// backward: v_p -= L(m, p)^T v_m for p < m (one CTA per tile p, warp per column)
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ S, int T, int nb,
+                                                     int m, double* __restrict__ v) {
+    extern __shared__ double sv[];
+    const double* vm = v + (long long)m * nb;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
+    __syncthreads();
+    if (!TRANS) {
+        const int i = m + 1 + blockIdx.x;
+        const double* __restrict__ A = S + tile_offset(i, m, T, nb);
+        double* vi = v + (long long)i * nb;
+        for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+            double acc = 0.0;
+            for (int c = 0; c < nb; ++c) acc = fma(A[r + (long long)c * nb], sv[c], acc);
+            vi[r] -= acc;
+        }
+    } else {
+        const int pt = blockIdx.x;
+        const double* __restrict__ A = S + tile_offset(m, pt, T, nb);
+        double* vp = v + (long long)pt * nb;
+        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+        for (int c = warp; c < nb; c += nw) {
+            double acc = 0.0;
+            for (int r = lane; r < nb; r += 32) acc = fma(A[r + (long long)c * nb], sv[r], acc);
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0) vp[c] -= acc;
+        }
+    }
+}
+
+int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans) {
+    const int T = g.T, nb = g.nb;
+    const size_t smem = (size_t)nb * sizeof(double);
+    const double tb = 8.0 * nb * nb;
+    int rc = 0;
+    L.begin(trans ? "trsv_backward" : "trsv_forward");
+    if (!trans) {
+        for (int m = 0; m < T; ++m) {
+            k_trsv_diag<false><<<1, 256, smem, L.stream>>>(S, T, nb, m, v);
+            L.count();
+            if (m + 1 < T) {
+                k_trsv_update<false><<<T - m - 1, 256, smem, L.stream>>>(S, T, nb, m, v);
+                L.count();
+            }
+        }
+    } else {
+        for (int m = T - 1; m >= 0; --m) {
+            k_trsv_diag<true><<<1, 256, smem, L.stream>>>(S, T, nb, m, v);
+            L.count();
+            if (m > 0) {
+                k_trsv_update<true><<<m, 256, smem, L.stream>>>(S, T, nb, m, v);
+                L.count();
+            }
+        }
+    }
+    // algorithmic: n_pad^2 flops (one multiply-add per stored lower entry), the lower triangle read once
+    const double ntri = (double)num_tiles(T);
+    rc = L.end((double)g.npad * g.npad, ntri * tb);
+    return rc;
+}
+
+// Per-tile partial of w^T M w over the lower tiles for M0 and M1 (off-diagonal tiles doubled,
+// since the upper tiles are their transposes); diagonal tiles are stored in full.
+__global__ void __launch_bounds__(256) k_qform(Geom g, const double* __restrict__ M0,
+                                               const double* __restrict__ M1,
+                                               const double* __restrict__ w,
+                                               double* __restrict__ slots) {
+    __shared__ double red[2][8];
+    const int T = g.T, nb = g.nb;
+    const long long t = blockIdx.x;
+    int j = (int)(((2.0 * T + 1.0) - sqrt((2.0 * T + 1.0) * (2.0 * T + 1.0) - 8.0 * (double)t)) * 0.5);
+    if (j < 0) j = 0;
+    while (j > 0 && tile_index(j, j, T) > t) --j;
+    while (j + 1 < T && tile_index(j + 1, j + 1, T) <= t) ++j;
+    const int i = j + (int)(t - tile_index(j, j, T));
+    const double* wi = w + (long long)i * nb;
+    const double* wj = w + (long long)j * nb;
+    const long long base = t * (long long)nb * nb;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    double a0 = 0.0, a1 = 0.0;
+    for (int c = warp; c < nb; c += 8) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int r = lane; r < nb; r += 32) {
+            const long long e = base + r + (long long)c * nb;
+            s0 = fma(M0[e], wi[r], s0);
+            s1 = fma(M1[e], wi[r], s1);
+        }
+        a0 = fma(s0, wj[c], a0);
+        a1 = fma(s1, wj[c], a1);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, off);
+        a1 += __shfl_down_sync(0xffffffffu, a1, off);
+    }
+    if (lane == 0) { red[0][warp] = a0; red[1][warp] = a1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < 8; ++q) { s0 += red[0][q]; s1 += red[1][q]; }
+        const double f = i == j ? 1.0 : 2.0;
+        slots[2 * t] = f * s0;
+        slots[2 * t + 1] = f * s1;
+    }
+}
+
+int launch_qform(Launcher& L, const Geom& g, const double* M0, const double* M1, const double* w,
+                 double* qform_slots) {
+    const long long tiles = num_tiles(g.T);
+    L.begin("qform");
+    k_qform<<<(unsigned)tiles, 256, 0, L.stream>>>(g, M0, M1, w, qform_slots);
+    L.count();
+    const double e = (double)tiles * g.nb * g.nb;
+    return L.end(4.0 * e, 16.0 * e);
+}
+
+// fixed-order block sum of src[0..count) with stride `stride` starting at `first`
+__device__ double block_sum(const double* __restrict__ src, long long count, int stride, int first,
+                            double* red) {
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < count; q += blockDim.x) s += src[q * stride + first];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_assemble(Geom g, const double* __restrict__ y,
+                                                   Slots s, int nstrips, int deriv,
+                                                   const ThetaConsts* __restrict__ tc,
+                                                   const int* __restrict__ status,
+                                                   EvalOut* __restrict__ out) {
+    __shared__ double red[1024];
+    __shared__ double sq[1024];
+    // y^T y (padding entries of y are zero)
+    double a = 0.0;
+    for (long long q = threadIdx.x; q < g.npad; q += blockDim.x) a = fma(y[q], y[q], a);
+    sq[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sq[threadIdx.x] += sq[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double quad = sq[0];
+    const double logdet = 2.0 * block_sum(s.logdet, g.T, 1, 0, red);
+    const double n = (double)g.n;
+    const double s2 = tc->sigma2;
+    double qa = 0, qn = 0, ta = 0, tn = 0, faa = 0, fan = 0, fnn = 0;
+    if (deriv) {
+        const long long tiles = num_tiles(g.T);
+        qa = block_sum(s.qform, tiles, 2, 0, red);
+        qn = block_sum(s.qform, tiles, 2, 1, red);
+        const long long nd = (long long)g.T * nstrips, no = tiles * nstrips;
+        ta = block_sum(s.diag, nd, 5, 0, red);
+        tn = block_sum(s.diag, nd, 5, 1, red);
+        faa = block_sum(s.diag, nd, 5, 2, red) + 2.0 * block_sum(s.offd, no, 3, 0, red);
+        fan = block_sum(s.diag, nd, 5, 3, red) + 2.0 * block_sum(s.offd, no, 3, 1, red);
+        fnn = block_sum(s.diag, nd, 5, 4, red) + 2.0 * block_sum(s.offd, no, 3, 2, red);
+    }
+    if (threadIdx.x == 0) {
+        out->logdet = logdet;
+        out->quad = quad;
+        out->loglik = -0.5 * n * 1.83787706640934548356 - 0.5 * logdet - 0.5 * quad;   // log(2 pi)
+        out->status = *status;
+        if (deriv) {
+            out->q_alpha = qa; out->q_nu = qn; out->t_alpha = ta; out->t_nu = tn;
+            out->f_aa = faa; out->f_an = fan; out->f_nn = fnn;
+            // Eq. 2 with Step 2's closed form for sigma^2
+            out->score[0] = (quad - n) / (2.0 * s2);
+            out->score[1] = -0.5 * ta + 0.5 * qa;
+            out->score[2] = -0.5 * tn + 0.5 * qn;
+            // Eq. 3: I_11 = n / (2 sigma^4), I_1j = tr(Sigma^-1 Sigma_j) / (2 sigma^2),
+            // I_ij = <B_i, B_j> / 2 for i, j in {alpha, nu}
+            double* F = out->fisher;
+            F[0] = n / (2.0 * s2 * s2);
+            F[1] = F[3] = ta / (2.0 * s2);
+            F[2] = F[6] = tn / (2.0 * s2);
+            F[4] = 0.5 * faa;
+            F[5] = F[7] = 0.5 * fan;
+            F[8] = 0.5 * fnn;
+        }
+    }
+}
+
+int launch_assemble(Launcher& L, const Geom& g, const double* y, const Slots& s, bool deriv,
+                    const ThetaConsts* tc, const int* status, EvalOut* out) {
+    L.begin("assemble");
+    k_assemble<<<1, 1024, 0, L.stream>>>(g, y, s, strips_per_tile(g.nb), deriv ? 1 : 0, tc, status, out);
+    L.count();
+    return L.end(0.0, 0.0);
+}
+
+}  // namespace fbt

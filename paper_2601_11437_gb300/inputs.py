@@ -91,6 +91,8 @@ WORKLOADS = {
                      description="FP64, n=400, theta_true=(1, 0.1, 0.5), start (0.5, 0.05, 1.0)"),
     "n16384": Workload("n16384", 16384, 1, (1.0, 0.1, 1.2), (0.5, 0.05, 0.8),
                        description="FP64, n=16384, theta_true=(1, 0.1, 1.2), start (0.5, 0.05, 0.8)"),
+    "n4096": Workload("n4096", 4096, 3, (1.0, 0.1, 1.2), (0.5, 0.05, 0.8),
+                      description="FP64, n=4096 (profiling-size case of the n=16384 workload)"),
     "n65536": Workload("n65536", 65536, 2, (1.0, 0.05, 0.8), (0.7, 0.035, 0.64),
                        description="n=65536, theta_true=(1, 0.05, 0.8), start theta_true*(0.7,0.7,0.8)"),
     "n32768": Workload("n32768", 32768, 5, (1.0, 0.1, 1.5), (1.0, 0.1, 1.5),

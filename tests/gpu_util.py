@@ -1,0 +1,43 @@
+"""Helpers for the GPU parity tests: library build/load, skips, and mapping the library's
+reordered lower-tile slabs back to dense matrices in the caller's order (data movement only)."""
+import os
+
+import numpy as np
+import pytest
+
+
+def have_gpu() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def require_gpu():
+    if not have_gpu():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2601_11437_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    _lib.load()
+
+
+def slab_to_dense(slab: np.ndarray, nb: int, T: int, n: int, lower_only: bool = False) -> np.ndarray:
+    """Lower-tile slab (column-major tiles, tile-column order) -> dense (n, n) matrix in the
+    library's (reordered) index order.  lower_only: return the lower triangle (a factor L);
+    otherwise mirror the lower triangle into the upper one (a symmetric matrix)."""
+    M = np.zeros((T * nb, T * nb))
+    t = 0
+    for j in range(T):
+        for i in range(j, T):
+            M[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = slab[t * nb * nb:(t + 1) * nb * nb].reshape(nb, nb).T
+            t += 1
+    low = np.tril(M)
+    M = low if lower_only else low + np.tril(M, -1).T
+    return M[:n, :n]
+
+
+def rel_err(a, b) -> float:
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
