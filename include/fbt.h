@@ -175,6 +175,35 @@ fbt_status fbt_copy_perm(fbt_ctx* ctx, long long* perm);
 /* Generate Sigma, Sigma_alpha, Sigma_nu at theta into the slabs without factorising (test hook). */
 fbt_status fbt_generate(fbt_ctx* ctx, const double theta[3], int with_derivatives);
 
+/*
+ * Allocation-free log-likelihood for small problems.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at the time they need l(theta),
+ * for example a process whose GPU memory another framework's allocator has already reserved,
+ * or a latency-critical loop that must not enter the CUDA allocator (cudaMalloc and cudaFree
+ * may synchronise the device).
+ *
+ * Computes the same l(theta) as mle_loglik (Algorithm 2, tile size 64, Z-order reordering) for
+ * n <= FBT_NOALLOC_MAX_N locations.  All scratch lives in one file-scope device array of
+ * 5 MiB inside libfbt.so, which every GPU that loads the library holds until the process exits;
+ * nothing is allocated or freed by this call (no cudaMalloc, cudaFree or allocating library
+ * routine).
+ *   locs, z           n x 2 row-major locations and n field values: device pointers on the
+ *                     current device if inputs_on_device != 0, else host pointers
+ *   theta, jitter     as for mle_loglik and fbt_opts.jitter (host values)
+ *   loglik            host pointer receiving l(theta) (-inf on FBT_ERR_DOMAIN / FBT_ERR_NOT_PD)
+ *   stream            cudaStream_t on the current device, or NULL; the call synchronises it
+ * Returns FBT_ERR_ARG for n < 1, n > FBT_NOALLOC_MAX_N, NULL pointers or a bad jitter.
+ * The first call on a device looks up the array's device address on that device (current at
+ * the time of the call); make that first call before any stream capture.  Every call uses the
+ * same array and leaves its contents behind for the next; calls whose device work overlaps
+ * (two host threads, or two streams not ordered with each other) race on it and must be
+ * serialised by the caller.
+ */
+#define FBT_NOALLOC_MAX_N 1024
+long long fbt_noalloc_max_n(void);
+fbt_status fbt_loglik_noalloc(const double* locs, const double* z, int inputs_on_device, long long n,
+                              const double theta[3], double jitter, double* loglik, void* stream);
+
 void fbt_destroy(fbt_ctx* ctx);
 const char* fbt_strerror(int status);
 const char* fbt_last_cuda_error(void);

@@ -56,6 +56,9 @@ SIGNATURES = {
     "fbt_copy_slab": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "fbt_copy_perm": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fbt_generate": (C.c_int, [C.c_void_p, c_double_p, C.c_int]),
+    "fbt_noalloc_max_n": (C.c_longlong, []),
+    "fbt_loglik_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_longlong, c_double_p, C.c_double,
+                                     c_double_p, C.c_void_p]),
     "fbt_destroy": (None, [C.c_void_p]),
     "fbt_strerror": (C.c_char_p, [C.c_int]),
     "fbt_last_cuda_error": (C.c_char_p, []),
