@@ -41,3 +41,28 @@ def slab_to_dense(slab: np.ndarray, nb: int, T: int, n: int, lower_only: bool = 
 def rel_err(a, b) -> float:
     a, b = np.asarray(a, float), np.asarray(b, float)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def tile_entry_index(r, c, nb: int, T: int):
+    """Flat slab index of entry (r, c), r >= c (arrays), in the library's lower-tile layout."""
+    r = np.asarray(r)
+    c = np.asarray(c)
+    i, j = r // nb, c // nb
+    t = j * T - j * (j - 1) // 2 + (i - j)
+    return t * nb * nb + (r % nb) + (c % nb) * nb
+
+
+def slab_lower_solve(slab: np.ndarray, nb: int, T: int, b: np.ndarray) -> np.ndarray:
+    """y = L^-1 b with L given as a lower-tile slab (host-side check of the device solve)."""
+    import scipy.linalg as sl
+    y = np.zeros(T * nb)
+    y[:len(b)] = b
+    for m in range(T):
+        t = m * T - m * (m - 1) // 2
+        Lmm = slab[t * nb * nb:(t + 1) * nb * nb].reshape(nb, nb).T
+        y[m * nb:(m + 1) * nb] = sl.solve_triangular(Lmm, y[m * nb:(m + 1) * nb], lower=True)
+        for i in range(m + 1, T):
+            ti = t + (i - m)
+            Lim = slab[ti * nb * nb:(ti + 1) * nb * nb].reshape(nb, nb).T
+            y[i * nb:(i + 1) * nb] -= Lim @ y[m * nb:(m + 1) * nb]
+    return y

@@ -164,3 +164,31 @@ def test_fisher_bt_run_matches_oracle_trajectory():
     assert st.loglik == pytest.approx(ref.loglik, rel=1e-10)
     if st.state == fbt.CONVERGED:
         assert np.linalg.norm(np.array(st.score[:])) <= 1e-3
+
+
+def test_l9_start_matches_oracle():
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(300, 14, (1.0, 0.1, 0.5))
+    lo, hi = (0.01, 0.01, 0.01), (5.0, 5.0, 2.0)
+    ctx = fbt.fbt_create(locs, z, nb=64)
+    st = fbt.fisher_bt_start(ctx, theta_lo=lo, theta_hi=hi)
+    ref = fisher_bt.start(likelihood.DenseEvaluator(locs, z), theta_lo=lo, theta_hi=hi)
+    np.testing.assert_array_equal(np.array(st.theta[:]), ref.theta)
+    assert (st.n_ll, st.n_grad, st.state) == (ref.n_ll, ref.n_grad, ref.state) == (10, 1, st.state)
+    assert st.loglik == pytest.approx(ref.loglik, rel=TOL_EVAL)
+
+
+def test_shift_to_nelder_mead_and_final_fisher(monkeypatch):
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(200, 15, (1.0, 0.1, 0.5))
+    bt = fbt.default_bt_opts()
+    bt.max_grad_calls = 1                 # force the shift after the second gradient call
+    ctx = fbt.fbt_create(locs, z, nb=64)
+    st = fbt.fisher_bt_run(ctx, theta0=(0.5, 0.05, 1.0), bt=bt)
+    monkeypatch.setattr(fisher_bt, "MAX_GRAD_CALLS", 1)
+    ref = fisher_bt.run(likelihood.DenseEvaluator(locs, z), theta0=(0.5, 0.05, 1.0))
+    assert st.state == fbt.DONE_NM and ref.state == fisher_bt.DONE_NM
+    np.testing.assert_allclose(np.array(st.theta[:]), ref.theta, rtol=1e-4)
+    assert st.loglik == pytest.approx(ref.loglik, rel=1e-8)
+    Iref = likelihood.loglik_score_fisher(locs, z, tuple(st.theta[:])).fisher
+    assert rel_err(np.array(st.fisher[:]).reshape(3, 3), Iref) < TOL_EVAL
