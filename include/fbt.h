@@ -57,7 +57,12 @@ typedef struct {
                           /* are permutation invariant, the reordering groups near locations     */
     int with_derivatives; /* 1 (default): workspace for mle_eval; 0: mle_loglik only             */
     int device;           /* CUDA device ordinal; default 0                                        */
+    int precision;        /* arithmetic of the tile updates: FBT_PREC_FP64 (default, FP64 DFMA)   */
+                          /* or FBT_PREC_FP64_EMULATED (FP64-accurate products on the BF16 tensor  */
+                          /* cores by 7-bit slicing; needs nb = 128)                              */
 } fbt_opts;
+
+enum { FBT_PREC_FP64 = 0, FBT_PREC_FP64_EMULATED = 1 };
 
 void fbt_default_opts(fbt_opts* opts);
 

@@ -112,6 +112,8 @@ struct fbt_ctx {
     int* status = nullptr;
     EvalOut* out = nullptr;
     double *S = nullptr, *SA = nullptr, *SN = nullptr;
+    unsigned char* slices = nullptr;         // digit planes of L (emulated-FP64 tile updates)
+    unsigned char* slice_scratch = nullptr;  // digit planes of transform panels / rows
     Profiler* prof = nullptr;
     long long launches = 0;
     long long h2d_bytes = 0, d2h_bytes = 0;
@@ -164,7 +166,16 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pS = take(slab);
     char* pSA = o.with_derivatives ? take(slab) : nullptr;
     char* pSN = o.with_derivatives ? take(slab) : nullptr;
+    // emulated FP64: digit planes of every strictly-lower tile of L (kept from the Cholesky for
+    // the two-sided transforms), plus scratch for two panels / rows and two diagonal tiles
+    const bool emu = o.precision == FBT_PREC_FP64_EMULATED;
+    const long long nL = T * (T - 1) / 2 > 0 ? T * (T - 1) / 2 : 1;
+    const long long nX = 2 * (T > 1 ? T - 1 : 1) + 2;
+    char* psl = emu ? take((size_t)nL * ozaki_tile_bytes()) : nullptr;
+    char* psx = emu && o.with_derivatives ? take((size_t)nX * ozaki_tile_bytes()) : nullptr;
     if (base && c) {
+        c->slices = (unsigned char*)psl;
+        c->slice_scratch = (unsigned char*)psx;
         c->X = (double*)pX; c->Y = (double*)pY; c->Z = (double*)pZ;
         c->vy = (double*)pvy; c->vw = (double*)pvw;
         c->perm = (long long*)pperm; c->bbox = (double*)pbbox;
@@ -178,7 +189,8 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
 }
 
 static bool opts_valid(const fbt_opts& o) {
-    return (o.nb == 64 || o.nb == 128) && o.jitter >= 0.0 && isfinite(o.jitter) && o.device >= 0;
+    return (o.nb == 64 || o.nb == 128) && o.jitter >= 0.0 && isfinite(o.jitter) && o.device >= 0 &&
+           (o.precision == FBT_PREC_FP64 || (o.precision == FBT_PREC_FP64_EMULATED && o.nb == 128));
 }
 
 extern "C" {
@@ -190,6 +202,7 @@ void fbt_default_opts(fbt_opts* o) {
     o->reorder = 1;
     o->with_derivatives = 1;
     o->device = 0;
+    o->precision = FBT_PREC_FP64;
 }
 
 size_t fbt_workspace_bytes(long long n, const fbt_opts* opts) {
@@ -303,7 +316,8 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
     if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN, deriv, c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
-    if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status))) return cuda_fail((cudaError_t)rc, "potrf");
+    if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices)))
+        return cuda_fail((cudaError_t)rc, "potrf");
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
     if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
     if (deriv) {
@@ -314,7 +328,8 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
         // written by the transform and must read as zero in the assembly
         CK(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
            "clear slots");
-        if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd)))
+        if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd, c->status,
+                               c->opts.precision, c->slices, c->slice_scratch)))
             return cuda_fail((cudaError_t)rc, "sygst");
     }
     if ((rc = launch_assemble(L, g, c->vy, c->slots, deriv, c->tc, c->status, c->out)))
@@ -323,6 +338,7 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     c->d2h_bytes += (long long)sizeof(EvalOut);
     CK(cudaStreamSynchronize(c->stream), "evaluation sync");
     if (c->prof) c->prof->flush();
+    if (c->host_out.status & ST_TIMEOUT) return FBT_ERR_TIMEOUT;
     if (c->host_out.status & ST_NOT_PD) return FBT_ERR_NOT_PD;
     if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
     return FBT_OK;

@@ -17,7 +17,10 @@
 namespace fbt {
 
 // ---- status bits set on the device (combined with atomicOr) ----
-enum : int { ST_NOT_PD = 1, ST_BESSEL = 2, ST_DOMAIN = 4 };
+enum : int { ST_NOT_PD = 1, ST_BESSEL = 2, ST_DOMAIN = 4, ST_TIMEOUT = 8 };
+
+// ---- arithmetic of the tile updates ----
+enum : int { PREC_FP64 = 0, PREC_FP64_OZAKI = 1 };
 
 // ---- trapezoid quadrature of K_nu, K_{nu-1} and dK_nu/dnu (see matern_gen.cu) ----
 constexpr int QUAD_LEVELS = 4;
@@ -69,6 +72,59 @@ __device__ inline void tri_decode(long long t, int& r, int& c) {
     c = (int)(t - rr * (rr + 1) / 2);
 }
 
+// ---- FP64-accurate tile updates on tensor cores (ozaki.cu) ----
+size_t ozaki_tile_bytes();   // digit planes + row scales of one sliced 128 x 128 tile
+// position of strictly-lower tile (i, k), i > k, in the column-ordered list of such tiles
+__host__ __device__ inline long long strict_lower_pos(int i, int k, int T) {
+    return tile_index(i, k, T) - k - 1;
+}
+
+// Which tiles a slicing launch reads: block t of the launch slices tile (ti, tj) of src into
+// position t of the slice buffer.
+enum : int { SLICE_PANEL = 0, SLICE_ROW = 1, SLICE_DIAG = 2 };
+struct SliceJob {
+    const double* src;
+    int mode, k, T;
+    __device__ void tile(int t, int& ti, int& tj) const {
+        if (mode == SLICE_PANEL) { ti = k + 1 + t; tj = k; }       // column k below the diagonal
+        else if (mode == SLICE_ROW) { ti = k; tj = t; }            // row k left of the diagonal
+        else { ti = k; tj = k; }                                    // diagonal tile k
+    }
+};
+
+// One CTA of an update launch: 128 rows x 32 columns of one target tile.
+enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3 };
+struct OzGemmJob {
+    int mode, k, T;
+    double* C;                     // target slab
+    const unsigned char* slA;      // sliced A operands
+    const unsigned char* slB;      // sliced B operands
+    size_t tile_bytes;
+    double mult;
+    __device__ void task(long long bid, const unsigned char*& sa, const unsigned char*& sb,
+                         double*& Ct, int& c0, double& m) const {
+        const long long tsk = bid >> 2;
+        c0 = (int)(bid & 3) * 32;
+        m = mult;
+        if (mode == OZ_POTRF_UPD || mode == OZ_SYGST_UPD) {
+            int ii, jj;
+            tri_decode(tsk, ii, jj);
+            Ct = C + tile_offset(k + 1 + ii, k + 1 + jj, T, 128);
+            sa = slA + (size_t)ii * tile_bytes;
+            sb = slB + (size_t)jj * tile_bytes;
+        } else if (mode == OZ_SYGST_FIX) {
+            Ct = C + tile_offset(k + 1 + (int)tsk, k, T, 128);
+            sa = slA + (size_t)tsk * tile_bytes;
+            sb = slB;
+        } else {                  // OZ_SYGST_ROWUPD, m = k: targets (i, kk), i > m > kk
+            const int kk = (int)(tsk % k), ii = (int)(tsk / k);
+            Ct = C + tile_offset(k + 1 + ii, kk, T, 128);
+            sa = slA + (size_t)ii * tile_bytes;
+            sb = slB + (size_t)kk * tile_bytes;
+        }
+    }
+};
+
 // ---- partial-sum slot layout (doubles) ----
 struct Slots {
     double* logdet;     // [T]               sum_j log L_jj of diagonal tile k
@@ -107,12 +163,22 @@ int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y
                     const ThetaConsts* tc, const QuadTables* qt, double* S, double* SA,
                     double* SN, bool deriv, int* status);
 
-// tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile
-int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status);
+int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntiles, bool rows,
+                       unsigned char* dst);
+int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
+                      const char* family);
+
+// tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile;
+// precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`)
+int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
+                 int precision = PREC_FP64, unsigned char* slices = nullptr);
 // two-sided transform B = L^-1 M L^-T of both derivative slabs in place, with the trace and
 // Frobenius-product partials of the result
+// precision PREC_FP64_OZAKI: L_slices holds the digit planes of every strictly-lower tile of L
+// (written by launch_potrf), scratch room for 2 (T - 1) + 2 more sliced tiles
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
-                 double* diag_slots, double* offd_slots);
+                 double* diag_slots, double* offd_slots, int* status, int precision = PREC_FP64,
+                 const unsigned char* L_slices = nullptr, unsigned char* scratch = nullptr);
 int strips_per_tile(int nb);
 
 // v <- L^-1 v (trans = false) or v <- L^-T v (trans = true), tile by tile

@@ -1,0 +1,288 @@
+// FP64-accurate tile updates on the BF16 tensor cores (tcgen05), by error-free slicing.
+//
+// A tile update C -= op(A) op(B) with K = nb = 128 is computed as follows (the splitting scheme
+// of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012, carried out on tensor cores):
+//  1. Slicing.  Every row r of an operand (the dimension that survives into C) is scaled by
+//     s_r = 2^E_r with |x| < s_r for all its entries, and the scaled values u in (-1, 1) are cut
+//     into S = 8 signed 7-bit digits: u = sum_p d_p 2^(-7(p+1)) + O(2^-56), |d_p| <= 127.
+//     Digits are exact in BF16, and the cut is exact in FP64 (scaling by 2^k, truncation).
+//  2. Products.  For digit planes A_p, B_q the product A_p B_q^T over K = 128 is a sum of
+//     integers bounded by 128 * 127^2 < 2^21, so FP32 accumulation in TMEM is exact; all products
+//     of one "weight" g = p + q (at most 8 of them) share one accumulator and stay exact
+//     (8 * 2^21 <= 2^24).  The 36 products with g <= 7 are kept; the dropped ones are below
+//     2^-56 relative per element product, i.e. below FP64 rounding of the K-term dot product.
+//  3. Recombination.  The 8 exact group sums are combined in 64-bit integers (two words), then
+//     converted to FP64, scaled by s_r s_c 2^(-7(g+2)) and subtracted from the FP64 C.
+// The MMA is tcgen05.mma kind::f16 (BF16 in, FP32 out) M = 128, N = 32, K = 16, operands in
+// shared memory (canonical K-major core-matrix layout, no swizzle) filled by bulk copies
+// (cp.async.bulk, 1-D) from a pre-sliced panel buffer; accumulators live in tensor memory.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fbt_kernels.cuh"
+
+namespace fbt {
+
+constexpr int OZ_S = 8;                      // digit planes per operand
+constexpr int OZ_G = 8;                      // accumulated weights g = 0..7
+constexpr int OZ_N = 32;                     // output columns per CTA
+constexpr int OZ_KC = 16;                    // K per pipeline stage (one MMA K-step)
+constexpr int OZ_NKC = 128 / OZ_KC;          // stages per K = 128
+constexpr int OZ_CHUNK = 128 * OZ_KC * 2;    // bytes of one plane chunk: 128 rows x 16 K bf16
+constexpr int OZ_PLANE = OZ_NKC * OZ_CHUNK;  // 32 KB: one plane of a 128 x 128 tile
+constexpr size_t OZ_TILE_BYTES = (size_t)OZ_S * OZ_PLANE;   // 256 KB of digits per tile
+constexpr int OZ_STAGE_A = OZ_S * OZ_CHUNK;                  // 32 KB
+constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 8 KB
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;
+constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits
+
+size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }
+
+// byte offset of digit (row, k) inside one plane of a sliced tile: chunk k/16, then the
+// canonical K-major core-matrix layout of a 128 x 16 block (LBO = 128 B, SBO = 256 B)
+__host__ __device__ inline uint32_t oz_off(int row, int k) {
+    return (uint32_t)((k >> 4) * OZ_CHUNK + (row & 7) * 16 + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (k & 7) * 2);
+}
+
+// ------------------------------------------------------------------------------------------
+// slicing: one CTA per tile, thread t handles (row, 8-wide k group) pairs
+//   ROWS = true : operand rows = tile rows, K = tile columns  (A = X, or B = X in C -= A X^T)
+//   ROWS = false: operand rows = tile columns, K = tile rows  (B = X in C -= A X)
+// ------------------------------------------------------------------------------------------
+template <bool ROWS>
+__global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ S, int T, int nb,
+                                                     SliceJob job, unsigned char* __restrict__ dst) {
+    __shared__ double s_scale[128];
+    __shared__ double s_inv[128];
+    const int t = blockIdx.x;
+    int ti, tj;
+    job.tile(t, ti, tj);
+    const double* X = job.src + tile_offset(ti, tj, T, nb);
+    unsigned char* out = dst + (size_t)t * (OZ_TILE_BYTES + 128 * sizeof(double));
+    double* scale_out = (double*)(out + OZ_TILE_BYTES);
+    // per operand row: the scale 2^E with max |x| < 2^E
+    for (int r = threadIdx.x; r < 128; r += blockDim.x) {
+        double m = 0.0;
+        for (int k = 0; k < 128; ++k) {
+            const double v = ROWS ? X[r + k * 128] : X[k + r * 128];
+            m = fmax(m, fabs(v));
+        }
+        int e = 0;
+        if (m > 0.0) e = ilogb(m) + 1;
+        s_scale[r] = ldexp(1.0, e);
+        s_inv[r] = ldexp(1.0, -e);
+        scale_out[r] = s_scale[r];
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < 128 * 16; w += blockDim.x) {
+        const int r = w & 127, k8 = (w >> 7) * 8;
+        uint32_t packed[OZ_S][4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            double u0 = (ROWS ? X[r + (k8 + j) * 128] : X[(k8 + j) + r * 128]) * s_inv[r];
+            double u1 = (ROWS ? X[r + (k8 + j + 1) * 128] : X[(k8 + j + 1) + r * 128]) * s_inv[r];
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) {
+                u0 *= 128.0;
+                u1 *= 128.0;
+                const double d0 = trunc(u0), d1 = trunc(u1);
+                u0 -= d0;
+                u1 -= d1;
+                const uint32_t b0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0));
+                const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
+                packed[p][j >> 1] = b0 | (b1 << 16);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+            uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+            *(uint4*)(out + (size_t)p * OZ_PLANE + oz_off(r, k8)) = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// PTX helpers
+// ------------------------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t oz_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;         // LBO: next 8-element K group
+    d |= (uint64_t)(256 >> 4) << 32;         // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    return d;
+}
+
+__device__ inline void mbar_init(uint64_t* b, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ inline bool mbar_wait(uint64_t* b, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < OZ_SPIN_LIMIT; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(smem_u32(b)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ inline void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ inline void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ inline void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------------------------------
+// the update kernel: one CTA = 128 rows x 32 columns of one C tile, 4 warps
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 2) k_ozaki_gemm(OzGemmJob job, int* status) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    unsigned char* stA = oz_smem;                                    // [2][32 KB]
+    unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [2][8 KB]
+    uint64_t* bars = (uint64_t*)(oz_smem + OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B));
+    uint64_t* full = bars;          // [2]
+    uint64_t* empty = bars + 2;     // [2]
+    uint64_t* done = bars + 4;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 6);
+    int* fail = (int*)(bars + 7);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const unsigned char *sa, *sb;
+    double* C;
+    int c0;
+    double mult;
+    job.task(blockIdx.x, sa, sb, C, c0, mult);
+    const double* scale_a = (const double*)(sa + OZ_TILE_BYTES);
+    const double* scale_b = (const double*)(sb + OZ_TILE_BYTES);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(OZ_G * OZ_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 32) {
+        // producer: digit chunks of A (128 rows) and B (rows c0 .. c0+31) for each K stage
+        for (int kc = 0; kc < OZ_NKC; ++kc) {
+            const int s = kc & 1;
+            if (kc >= OZ_STAGES && !mbar_wait(&empty[s], ((kc >> 1) - 1) & 1)) { atomicOr(fail, 1); break; }
+            mbar_expect_tx(&full[s], OZ_STAGE_A + OZ_STAGE_B);
+            for (int p = 0; p < OZ_S; ++p) {
+                bulk_g2s(stA + s * OZ_STAGE_A + p * OZ_CHUNK, sa + (size_t)p * OZ_PLANE + kc * OZ_CHUNK, OZ_CHUNK, &full[s]);
+                bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
+                         sb + (size_t)p * OZ_PLANE + kc * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
+            }
+        }
+    } else if (tid == 0) {
+        // MMA issuer: for each stage, the 36 digit products with p + q <= 7 into group g = p + q
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_N >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+        for (int kc = 0; kc < OZ_NKC; ++kc) {
+            const int s = kc & 1;
+            if (!mbar_wait(&full[s], (kc >> 1) & 1)) { atomicOr(fail, 2); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
+            for (int p = 0; p < OZ_S; ++p)
+                for (int q = 0; p + q < OZ_G; ++q) {
+                    const int g = p + q;
+                    const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
+                    mma_bf16(tmem + g * OZ_N, oz_desc(a0 + p * OZ_CHUNK), oz_desc(b0 + q * (OZ_N * OZ_KC * 2)), idesc, acc);
+                }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);
+    }
+    __syncthreads();      // role loops are done issuing; *fail is visible to every thread
+    // epilogue: every thread owns one row of the 128 x 32 block
+    const bool ok = *fail == 0 && mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int r = warp * 32 + lane;
+        const double sr = scale_a[r] * mult;
+        for (int cb = 0; cb < OZ_N; cb += 8) {
+            long long hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
+#pragma unroll
+            for (int g = 0; g < OZ_G; ++g) {
+                float v[8];
+                tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + g * OZ_N + cb, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long iv = (long long)__float2int_rn(v[j]);
+                    if (g < 4) hi[j] += iv * (1ll << (7 * (3 - g)));
+                    else lo[j] += iv * (1ll << (7 * (7 - g)));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + cb + j;
+                const double val = fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63);
+                double* cp = C + r + (long long)c * 128;
+                *cp -= sr * scale_b[c] * val;
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_G * OZ_N));
+    }
+}
+
+int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntiles, bool rows,
+                       unsigned char* dst) {
+    if (ntiles <= 0) return 0;
+    L.begin("ozaki_slice");
+    if (rows) k_ozaki_slice<true><<<ntiles, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
+    else k_ozaki_slice<false><<<ntiles, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
+    L.count();
+    return L.end(0.0, (double)ntiles * (128.0 * 128 * 8 + OZ_TILE_BYTES));
+}
+
+int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
+                      const char* family) {
+    if (ctas <= 0) return 0;
+    cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    L.begin(family);
+    k_ozaki_gemm<<<(unsigned)ctas, 128, OZ_SMEM, L.stream>>>(job, status);
+    L.count();
+    return L.end(flops, 0.0);
+}
+
+}  // namespace fbt

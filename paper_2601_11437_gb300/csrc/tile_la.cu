@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(256) k_gemm_tile(GemmParams p) {
 // host orchestration
 // ------------------------------------------------------------------------------------------
 template <int NB>
-static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status) {
+static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
+                      int precision, unsigned char* slices) {
     const int T = g.T;
     const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
     const size_t smem_trsm1 = (size_t)STRIP * (NB + 1) * sizeof(double);
@@ -328,22 +329,117 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
         k_trsm_strip<NB, false, 1, 0><<<m * NS, 256, smem_trsm1, L.stream>>>(tp);
         L.count();
         if ((rc = L.end((double)m * nb3, 16.0 * m * NB * NB))) return rc;
-        GemmParams gp{GEMM_POTRF_UPD, k, T, S, nullptr, nullptr};
         const long long tasks = (long long)m * (m + 1) / 2;
+        // algorithmic flops: 2 nb^3 per off-diagonal tile, nb^3 + nb^2 for a diagonal (SYRK) tile
+        const double fl = (double)m * (m - 1) / 2 * 2.0 * nb3 + m * (nb3 + (double)NB * NB);
+        if (NB == 128 && precision == PREC_FP64_OZAKI) {
+            // digit planes of panel k, kept for the two-sided transforms
+            unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * ozaki_tile_bytes();
+            SliceJob sj{S, SLICE_PANEL, k, T};
+            if ((rc = launch_ozaki_slice(L, g, sj, m, true, panel))) return rc;
+            OzGemmJob oj{OZ_POTRF_UPD, k, T, S, panel, panel, ozaki_tile_bytes(), 1.0};
+            if ((rc = launch_ozaki_gemm(L, oj, tasks * 4, fl, status, "ozaki_potrf_update"))) return rc;
+            continue;
+        }
+        GemmParams gp{GEMM_POTRF_UPD, k, T, S, nullptr, nullptr};
         L.begin("gemm_potrf_update");
         k_gemm_tile<NB, false, 1><<<dim3((unsigned)(tasks * SB * SB), 1), 256, 0, L.stream>>>(gp);
         L.count();
-        // algorithmic flops: 2 nb^3 per off-diagonal tile, nb^3 + nb^2 for a diagonal (SYRK) tile
-        const double fl = (double)m * (m - 1) / 2 * 2.0 * nb3 + m * (nb3 + (double)NB * NB);
         if ((rc = L.end(fl, 8.0 * NB * NB * (3.0 * tasks)))) return rc;
     }
     return rc;
 }
 
-int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status) {
-    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status);
-    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status);
+int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
+                 int precision, unsigned char* slices) {
+    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices);
+    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices);
     return cudaErrorInvalidValue;
+}
+
+// Two-sided transform with the GEMM-shaped updates on tensor cores (emulated FP64).
+static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
+                       double* diag_slots, double* offd_slots, int* status,
+                       const unsigned char* LS, unsigned char* scratch) {
+    constexpr int NB = 128, NS = NB / STRIP;
+    const int T = g.T;
+    const size_t tb = ozaki_tile_bytes();
+    const size_t smem2 = (size_t)2 * STRIP * (NB + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_trsm_strip<NB, false, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    const double nb3 = (double)NB * NB * NB;
+    const double tbytes = 8.0 * NB * NB;
+    unsigned char* X0 = scratch;                                  // E panel / row of M0
+    unsigned char* X1 = scratch + (size_t)(T > 1 ? T - 1 : 1) * tb; // E panel / row of M1
+    unsigned char* D0 = scratch + (size_t)2 * (T > 1 ? T - 1 : 1) * tb;
+    unsigned char* D1 = D0 + tb;
+    double* M[2] = {M0, M1};
+    unsigned char* Xs[2] = {X0, X1};
+    unsigned char* Ds[2] = {D0, D1};
+    int rc = 0;
+    for (int k = 0; k < T; ++k) {
+        TrsmParams tp{TRSM_SYGST_DIAG_R, k, T, S, M0, M1, diag_slots};
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, false, 2, 0><<<NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        tp.mode = TRSM_SYGST_DIAG_L;
+        k_trsm_strip<NB, true, 2, 1><<<NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(4.0 * nb3, 6.0 * tbytes))) return rc;
+        const int m = T - k - 1;
+        if (m == 0) break;
+        tp.mode = TRSM_SYGST_PANEL;
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, false, 2, 0><<<m * NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tbytes))) return rc;
+        const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
+        for (int q = 0; q < 2; ++q) {
+            SliceJob dj{M[q], SLICE_DIAG, k, T};
+            if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
+        }
+        const double fix_fl = m * 2.0 * nb3;
+        for (int q = 0; q < 2; ++q) {      // E_ik = C_ik - 1/2 L_ik B_kk
+            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5};
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 4, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+        }
+        for (int q = 0; q < 2; ++q) {
+            SliceJob ej{M[q], SLICE_PANEL, k, T};
+            if ((rc = launch_ozaki_slice(L, g, ej, m, true, Xs[q]))) return rc;
+        }
+        const long long tasks = (long long)m * (m + 1) / 2;
+        for (int q = 0; q < 2; ++q) {      // M_ij -= L_ik E_jk^T + E_ik L_jk^T
+            OzGemmJob t1{OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0};
+            if ((rc = launch_ozaki_gemm(L, t1, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+            OzGemmJob t2{OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0};
+            if ((rc = launch_ozaki_gemm(L, t2, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+        }
+        for (int q = 0; q < 2; ++q) {      // P_ik = E_ik - 1/2 L_ik B_kk
+            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5};
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 4, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+        }
+    }
+    for (int m = 1; m < T; ++m) {
+        TrsmParams tp{TRSM_SYGST_ROW, m, T, S, M0, M1, offd_slots};
+        L.begin("trsm_sygst");
+        k_trsm_strip<NB, true, 2, 2><<<m * NS, 256, smem2, L.stream>>>(tp);
+        L.count();
+        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tbytes))) return rc;
+        const int below = T - m - 1;
+        if (below == 0) continue;
+        const unsigned char* Lp = LS + strict_lower_pos(m + 1, m, T) * tb;
+        for (int q = 0; q < 2; ++q) {
+            SliceJob rj{M[q], SLICE_ROW, m, T};
+            if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
+        }
+        const long long tasks = (long long)below * m;
+        for (int q = 0; q < 2; ++q) {      // M_(i,kk) -= L_(i,m) M_(m,kk)
+            OzGemmJob j{OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0};
+            if ((rc = launch_ozaki_gemm(L, j, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_rowupd"))) return rc;
+        }
+    }
+    return rc;
 }
 
 template <int NB>
@@ -412,7 +508,10 @@ static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, d
 }
 
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
-                 double* diag_slots, double* offd_slots) {
+                 double* diag_slots, double* offd_slots, int* status, int precision,
+                 const unsigned char* L_slices, unsigned char* scratch) {
+    if (g.nb == 128 && precision == PREC_FP64_OZAKI)
+        return sygst_ozaki(L, g, S, M0, M1, diag_slots, offd_slots, status, L_slices, scratch);
     if (g.nb == 128) return sygst_impl<128>(L, g, S, M0, M1, diag_slots, offd_slots);
     if (g.nb == 64) return sygst_impl<64>(L, g, S, M0, M1, diag_slots, offd_slots);
     return cudaErrorInvalidValue;

@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[0, 1], ids=["fp64", "fp64_emulated"])
+def full(request):
     require_gpu()
     import paper_2601_11437_gb300 as fbt
     w = inputs.WORKLOADS["n16384"]
@@ -27,7 +27,7 @@ def full():
     meta = json.load(open(os.path.join(ROOT, "tests", "golden", "fields", "n16384_z.json")))
     assert hashlib.sha256(np.ascontiguousarray(locs, dtype="<f8").tobytes()).hexdigest() == meta["locations_sha256"]
     z = np.load(os.path.join(ROOT, "tests", "golden", "fields", "n16384_z.npy"))
-    ctx = fbt.fbt_create(locs, z, nb=128)
+    ctx = fbt.fbt_create(locs, z, nb=128, precision=request.param)
     yield fbt, w, locs, z, ctx
     fbt.fbt_destroy(ctx)
 

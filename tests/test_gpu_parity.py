@@ -64,12 +64,12 @@ def test_padding_is_identity():
         np.testing.assert_array_equal(d[n:, :], 0.0)
 
 
-@pytest.mark.parametrize("n,nb", [(63, 64), (257, 64), (400, 128)])
-def test_cholesky_factor_matches_oracle(n, nb):
+@pytest.mark.parametrize("n,nb,precision", [(63, 64, 0), (257, 64, 0), (400, 128, 0), (400, 128, 1), (1000, 128, 1)])
+def test_cholesky_factor_matches_oracle(n, nb, precision):
     import paper_2601_11437_gb300 as fbt
     locs, z = field(n, 5)
     theta = (1.0, 0.1, 0.5)
-    ctx = fbt.fbt_create(locs, z, nb=nb, with_derivatives=False)
+    ctx = fbt.fbt_create(locs, z, nb=nb, with_derivatives=False, precision=precision)
     ll = fbt.mle_loglik(ctx, theta)
     perm = fbt.fbt_copy_perm(ctx)
     S = matern.covariance(locs[perm], theta, partials=False)["S"]
@@ -88,11 +88,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
 @pytest.mark.parametrize("name,n,seed,theta_true,theta,nb", CASES, ids=[c[0] for c in CASES])
-def test_loglik_score_fisher_match_oracle(name, n, seed, theta_true, theta, nb):
+def test_loglik_score_fisher_match_oracle(name, n, seed, theta_true, theta, nb, precision):
     import paper_2601_11437_gb300 as fbt
+    if precision == 1:
+        nb = 128           # the emulated path works on 128 x 128 tiles
     locs, z = field(n, seed, theta_true)
-    ctx = fbt.fbt_create(locs, z, nb=nb)
+    ctx = fbt.fbt_create(locs, z, nb=nb, precision=precision)
     ll, g, I = fbt.mle_eval(ctx, theta)
     ref = likelihood.loglik_score_fisher(locs, z, theta)
     assert ll == pytest.approx(ref.loglik, rel=TOL_EVAL)
@@ -150,12 +153,13 @@ def test_set_field_and_device_inputs():
     assert fbt.mle_loglik(ctx, theta) == pytest.approx(likelihood.loglik(locs, z2, theta), rel=TOL_EVAL)
 
 
-def test_fisher_bt_run_matches_oracle_trajectory():
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
+def test_fisher_bt_run_matches_oracle_trajectory(precision):
     import paper_2601_11437_gb300 as fbt
     w = inputs.WORKLOADS["n400"]
     locs = w.locations()
     z = fields.sample_field(locs, w.normals(), w.theta_true)
-    ctx = fbt.fbt_create(locs, z, nb=128)
+    ctx = fbt.fbt_create(locs, z, nb=128, precision=precision)
     st = fbt.fisher_bt_run(ctx, theta0=w.theta0)
     ref = fisher_bt.run(likelihood.DenseEvaluator(locs, z), theta0=w.theta0)
     assert st.state == ref.state
