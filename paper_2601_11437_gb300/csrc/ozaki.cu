@@ -38,12 +38,14 @@ constexpr int OZ_STAGES = 2;
 constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;
 constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits
 
-size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }
+size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }   // digits + row exponents
 
-// byte offset of digit (row, k) inside one plane of a sliced tile: chunk k/16, then the
-// canonical K-major core-matrix layout of a 128 x 16 block (LBO = 128 B, SBO = 256 B)
-__host__ __device__ inline uint32_t oz_off(int row, int k) {
-    return (uint32_t)((k >> 4) * OZ_CHUNK + (row & 7) * 16 + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (k & 7) * 2);
+// byte offset of digit (row, k) of plane p inside a sliced tile: K chunk k/16 (all 8 planes of a
+// chunk are contiguous, so one bulk copy fetches an A stage), plane p, then the canonical K-major
+// core-matrix layout of a 128 x 16 block (LBO = 128 B, SBO = 256 B)
+__host__ __device__ inline uint32_t oz_off(int p, int row, int k) {
+    return (uint32_t)((k >> 4) * (OZ_S * OZ_CHUNK) + p * OZ_CHUNK + (row & 7) * 16 + (row >> 3) * 256 +
+                      ((k >> 3) & 1) * 128 + (k & 7) * 2);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -54,51 +56,58 @@ __host__ __device__ inline uint32_t oz_off(int row, int k) {
 template <bool ROWS>
 __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ S, int T, int nb,
                                                      SliceJob job, unsigned char* __restrict__ dst) {
-    __shared__ double s_scale[128];
-    __shared__ double s_inv[128];
-    const int t = blockIdx.x;
+    // 4 CTAs per tile, 32 operand rows each; the digits are taken from the FP64 bit fields:
+    // |x| / 2^E_r = F 2^-56 with F = floor of the scaled magnitude (exact), digit p = bits
+    // 55-7p .. 49-7p of F with the sign of x -- the same digits as repeated truncation of
+    // u * 128 in FP64, without FP64 arithmetic.
+    __shared__ int s_exp[32];
+    const int t = blockIdx.x >> 2, rq = (blockIdx.x & 3) * 32;
     int ti, tj;
     job.tile(t, ti, tj);
     const double* X = job.src + tile_offset(ti, tj, T, nb);
     unsigned char* out = dst + (size_t)t * (OZ_TILE_BYTES + 128 * sizeof(double));
-    double* scale_out = (double*)(out + OZ_TILE_BYTES);
-    // per operand row: the scale 2^E with max |x| < 2^E
-    for (int r = threadIdx.x; r < 128; r += blockDim.x) {
-        double m = 0.0;
+    int* exp_out = (int*)(out + OZ_TILE_BYTES);
+    if (threadIdx.x < 32) {
+        const int r = rq + threadIdx.x;
+        unsigned long long mbits = 0;
         for (int k = 0; k < 128; ++k) {
             const double v = ROWS ? X[r + k * 128] : X[k + r * 128];
-            m = fmax(m, fabs(v));
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+            mbits = b > mbits ? b : mbits;          // |x| order = integer order of the bits
         }
-        int e = 0;
-        if (m > 0.0) e = ilogb(m) + 1;
-        s_scale[r] = ldexp(1.0, e);
-        s_inv[r] = ldexp(1.0, -e);
-        scale_out[r] = s_scale[r];
+        const int E = (int)(mbits >> 52);
+        const int e = E == 0 ? 0 : E - 1022;        // 2^(e-1) <= max |x| < 2^e (zero row: e = 0)
+        s_exp[threadIdx.x] = e;
+        exp_out[r] = e;
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < 128 * 16; w += blockDim.x) {
-        const int r = w & 127, k8 = (w >> 7) * 8;
+    for (int w = threadIdx.x; w < 32 * 16; w += blockDim.x) {
+        const int rl = w & 31, r = rq + rl, k8 = (w >> 5) * 8;
+        const int e = s_exp[rl];
         uint32_t packed[OZ_S][4];
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            double u0 = (ROWS ? X[r + (k8 + j) * 128] : X[(k8 + j) + r * 128]) * s_inv[r];
-            double u1 = (ROWS ? X[r + (k8 + j + 1) * 128] : X[(k8 + j + 1) + r * 128]) * s_inv[r];
+        for (int j = 0; j < 8; ++j) {
+            const double v = ROWS ? X[r + (k8 + j) * 128] : X[(k8 + j) + r * 128];
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            const int E = (int)((b >> 52) & 0x7FF);
+            const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+            const int sh = 1019 + e - E;            // F = M * 2^(E - 1075 - e + 56)
+            unsigned long long F = 0;
+            if (E != 0) F = sh < 0 ? (M << (-sh)) : (sh < 64 ? (M >> sh) : 0ull);
+            const bool neg = (b >> 63) != 0;
 #pragma unroll
             for (int p = 0; p < OZ_S; ++p) {
-                u0 *= 128.0;
-                u1 *= 128.0;
-                const double d0 = trunc(u0), d1 = trunc(u1);
-                u0 -= d0;
-                u1 -= d1;
-                const uint32_t b0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0));
-                const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1));
-                packed[p][j >> 1] = b0 | (b1 << 16);
+                int d = (int)((F >> (49 - 7 * p)) & 127ull);
+                d = neg ? -d : d;
+                const uint32_t h = __float_as_uint((float)d) >> 16;    // exact: |d| <= 127
+                if (j & 1) packed[p][j >> 1] |= h << 16;
+                else packed[p][j >> 1] = h;
             }
         }
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p) {
             uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
-            *(uint4*)(out + (size_t)p * OZ_PLANE + oz_off(r, k8)) = v;
+            *(uint4*)(out + oz_off(p, r, k8)) = v;
         }
     }
 }
@@ -155,9 +164,24 @@ __device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
 }
 
 // ------------------------------------------------------------------------------------------
-// the update kernel: one CTA = 128 rows x 32 columns of one C tile, 4 warps
+// the update kernel: one CTA = 128 rows x 32 columns of one target tile, 8 warps
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 2) k_ozaki_gemm(OzGemmJob job, int* status) {
+__device__ inline void tmem_ld8x(uint32_t taddr, uint32_t r[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// y * 2^s for finite y, by exponent arithmetic when the result stays normal
+__device__ inline double scale_pow2(double y, int s) {
+    if (y == 0.0) return 0.0;
+    const long long b = __double_as_longlong(y);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E + s >= 1 && E + s <= 2046) return __longlong_as_double(b + ((long long)s << 52));
+    return ldexp(y, s);
+}
+
+__global__ void __launch_bounds__(256, 2) k_ozaki_gemm(OzGemmJob job, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
     unsigned char* stA = oz_smem;                                    // [2][32 KB]
     unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [2][8 KB]
@@ -174,8 +198,8 @@ __global__ void __launch_bounds__(128, 2) k_ozaki_gemm(OzGemmJob job, int* statu
     int c0;
     double mult;
     job.task(blockIdx.x, sa, sb, C, c0, mult);
-    const double* scale_a = (const double*)(sa + OZ_TILE_BYTES);
-    const double* scale_b = (const double*)(sb + OZ_TILE_BYTES);
+    const int* exp_a = (const int*)(sa + OZ_TILE_BYTES);
+    const int* exp_b = (const int*)(sb + OZ_TILE_BYTES);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -194,16 +218,16 @@ __global__ void __launch_bounds__(128, 2) k_ozaki_gemm(OzGemmJob job, int* statu
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 32) {
-        // producer: digit chunks of A (128 rows) and B (rows c0 .. c0+31) for each K stage
+        // producer: one bulk copy for the 8 A planes of a K chunk, 8 for the B rows c0 .. c0+31
         for (int kc = 0; kc < OZ_NKC; ++kc) {
             const int s = kc & 1;
             if (kc >= OZ_STAGES && !mbar_wait(&empty[s], ((kc >> 1) - 1) & 1)) { atomicOr(fail, 1); break; }
             mbar_expect_tx(&full[s], OZ_STAGE_A + OZ_STAGE_B);
-            for (int p = 0; p < OZ_S; ++p) {
-                bulk_g2s(stA + s * OZ_STAGE_A + p * OZ_CHUNK, sa + (size_t)p * OZ_PLANE + kc * OZ_CHUNK, OZ_CHUNK, &full[s]);
+            const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
+            bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, OZ_STAGE_A, &full[s]);
+            for (int p = 0; p < OZ_S; ++p)
                 bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
-                         sb + (size_t)p * OZ_PLANE + kc * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
-            }
+                         sb + chunk + p * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
         }
     } else if (tid == 0) {
         // MMA issuer: for each stage, the 36 digit products with p + q <= 7 into group g = p + q
@@ -225,34 +249,36 @@ __global__ void __launch_bounds__(128, 2) k_ozaki_gemm(OzGemmJob job, int* statu
         mma_commit(done);
     }
     __syncthreads();      // role loops are done issuing; *fail is visible to every thread
-    // epilogue: every thread owns one row of the 128 x 32 block
     const bool ok = *fail == 0 && mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int r = warp * 32 + lane;
-        const double sr = scale_a[r] * mult;
-        for (int cb = 0; cb < OZ_N; cb += 8) {
-            long long hi[8], lo[8];
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), columns
+        // 16 (w / 4) .. +15 of each of the 8 group accumulators
+        const int r = (warp & 3) * 32 + lane;
+        const int cbase = (warp >> 2) * 16;
+        const int er = exp_a[r];
+        const bool negm = mult < 0.0;
+        const int em = ilogb(fabs(mult));            // |mult| is a power of two (1 or 1/2)
+        for (int cb = cbase; cb < cbase + 16; cb += 8) {
+            uint32_t v[OZ_G][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
-#pragma unroll
-            for (int g = 0; g < OZ_G; ++g) {
-                float v[8];
-                tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + g * OZ_N + cb, v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const long long iv = (long long)__float2int_rn(v[j]);
-                    if (g < 4) hi[j] += iv * (1ll << (7 * (3 - g)));
-                    else lo[j] += iv * (1ll << (7 * (7 - g)));
-                }
-            }
+            for (int g = 0; g < OZ_G; ++g)
+                tmem_ld8x(tmem + ((uint32_t)((warp & 3) * 32) << 16) + g * OZ_N + cb, v[g]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
+                // exact group sums (|.| < 2^24) -> fixed point with unit 2^-46:
+                // sum_g acc_g 2^(-7(g+2)) = (sum_(g<4) acc_g 2^(32-7g) + floor(sum_(g>=4) acc_g 2^(49-7g) / 2^17)) 2^-46
+                long long hi = 0, lo = 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
+#pragma unroll
+                for (int g = 4; g < OZ_G; ++g) lo += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (49 - 7 * g));
+                const long long fx = hi + (lo >> 17);
                 const int c = c0 + cb + j;
-                const double val = fma((double)hi[j], 0x1p-35, (double)lo[j] * 0x1p-63);
+                double y = scale_pow2((double)fx, er + exp_b[c] - 46 + em);
                 double* cp = C + r + (long long)c * 128;
-                *cp -= sr * scale_b[c] * val;
+                *cp = negm ? *cp + y : *cp - y;
             }
         }
     } else if (tid == 0) {
@@ -269,8 +295,8 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
                        unsigned char* dst) {
     if (ntiles <= 0) return 0;
     L.begin("ozaki_slice");
-    if (rows) k_ozaki_slice<true><<<ntiles, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
-    else k_ozaki_slice<false><<<ntiles, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
+    if (rows) k_ozaki_slice<true><<<ntiles * 4, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
+    else k_ozaki_slice<false><<<ntiles * 4, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
     L.count();
     return L.end(0.0, (double)ntiles * (128.0 * 128 * 8 + OZ_TILE_BYTES));
 }
@@ -280,7 +306,7 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
     if (ctas <= 0) return 0;
     cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
     L.begin(family);
-    k_ozaki_gemm<<<(unsigned)ctas, 128, OZ_SMEM, L.stream>>>(job, status);
+    k_ozaki_gemm<<<(unsigned)ctas, 256, OZ_SMEM, L.stream>>>(job, status);
     L.count();
     return L.end(flops, 0.0);
 }
