@@ -92,7 +92,7 @@ struct SliceJob {
     }
 };
 
-// One CTA of an update launch: 128 rows x 32 columns of one target tile.
+// One task of an update launch: 128 rows x 64 columns of one target tile (two per tile).
 enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3 };
 struct OzGemmJob {
     int mode, k, T;
@@ -101,10 +101,11 @@ struct OzGemmJob {
     const unsigned char* slB;      // sliced B operands
     size_t tile_bytes;
     double mult;
+    int assign;                    // 1: C = -mult * A B^T (overwrite); 0: C -= mult * A B^T
     __device__ void task(long long bid, const unsigned char*& sa, const unsigned char*& sb,
                          double*& Ct, int& c0, double& m) const {
-        const long long tsk = bid >> 2;
-        c0 = (int)(bid & 3) * 32;
+        const long long tsk = bid >> 1;
+        c0 = (int)(bid & 1) * 64;
         m = mult;
         if (mode == OZ_POTRF_UPD || mode == OZ_SYGST_UPD) {
             int ii, jj;

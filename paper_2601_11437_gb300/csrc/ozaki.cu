@@ -26,16 +26,16 @@ namespace fbt {
 
 constexpr int OZ_S = 8;                      // digit planes per operand
 constexpr int OZ_G = 8;                      // accumulated weights g = 0..7
-constexpr int OZ_N = 32;                     // output columns per CTA
+constexpr int OZ_N = 64;                     // output columns per task (TMEM: 8 groups x 64 = 512 cols)
 constexpr int OZ_KC = 16;                    // K per pipeline stage (one MMA K-step)
 constexpr int OZ_NKC = 128 / OZ_KC;          // stages per K = 128
 constexpr int OZ_CHUNK = 128 * OZ_KC * 2;    // bytes of one plane chunk: 128 rows x 16 K bf16
 constexpr int OZ_PLANE = OZ_NKC * OZ_CHUNK;  // 32 KB: one plane of a 128 x 128 tile
 constexpr size_t OZ_TILE_BYTES = (size_t)OZ_S * OZ_PLANE;   // 256 KB of digits per tile
 constexpr int OZ_STAGE_A = OZ_S * OZ_CHUNK;                  // 32 KB
-constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 8 KB
-constexpr int OZ_STAGES = 2;
-constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;
+constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 16 KB
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;   // 193 KB
 constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits
 
 size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }   // digits + row exponents
@@ -172,34 +172,38 @@ __device__ inline void tmem_ld8x(uint32_t taddr, uint32_t r[8]) {
                  : "r"(taddr));
 }
 
-// y * 2^s for finite y, by exponent arithmetic when the result stays normal
-__device__ inline double scale_pow2(double y, int s) {
-    if (y == 0.0) return 0.0;
+// (double)fx * 2^s, with the power of two applied by exponent arithmetic when the result stays
+// normal (fx == 0 gives 0; the rare out-of-range case falls back to ldexp)
+__device__ inline double fx_to_double(long long fx, int s) {
+    if (fx == 0) return 0.0;
+    const double y = (double)fx;
     const long long b = __double_as_longlong(y);
     const int E = (int)((b >> 52) & 0x7FF);
     if (E + s >= 1 && E + s <= 2046) return __longlong_as_double(b + ((long long)s << 52));
     return ldexp(y, s);
 }
 
-__global__ void __launch_bounds__(256, 2) k_ozaki_gemm(OzGemmJob job, int* status) {
-    extern __shared__ __align__(1024) unsigned char oz_smem[];
-    unsigned char* stA = oz_smem;                                    // [2][32 KB]
-    unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [2][8 KB]
-    uint64_t* bars = (uint64_t*)(oz_smem + OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B));
-    uint64_t* full = bars;          // [2]
-    uint64_t* empty = bars + 2;     // [2]
-    uint64_t* done = bars + 4;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 6);
-    int* fail = (int*)(bars + 7);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// Persistent (one CTA per SM), warp-specialised: warp 0 issues the MMAs, warp 1 streams digit
+// stages with bulk copies (4-stage ring), warps 2..9 drain the TMEM accumulators (warp w reads
+// TMEM lanes 32 (w % 4) .. +31, columns 32 ((w - 2) / 4) .. +31).  The accumulators are released
+// as soon as they are folded into 64-bit fixed point in registers, so the next task's MMAs run
+// while the epilogue converts and updates C in FP64.  N = 64 because an M = 128 MMA costs the
+// same issue time for any N <= 64 (measured on GB300), and TMEM holds 8 groups x 64 columns.
+constexpr int OZ_THREADS = 320;
+constexpr int OZ_EPI_WARPS = 8;
 
-    const unsigned char *sa, *sb;
-    double* C;
-    int c0;
-    double mult;
-    job.task(blockIdx.x, sa, sb, C, c0, mult);
-    const int* exp_a = (const int*)(sa + OZ_TILE_BYTES);
-    const int* exp_b = (const int*)(sb + OZ_TILE_BYTES);
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, long long ntasks, int* status) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    unsigned char* stA = oz_smem;                                    // [4][32 KB]
+    unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [4][16 KB]
+    uint64_t* bars = (uint64_t*)(oz_smem + OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B));
+    uint64_t* full = bars;                   // [4] stage loaded
+    uint64_t* empty = bars + OZ_STAGES;      // [4] stage consumed by the MMAs
+    uint64_t* tfull = bars + 2 * OZ_STAGES;  // accumulators complete
+    uint64_t* tempty = tfull + 1;            // accumulators drained into registers
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    int* fail = (int*)(tempty + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -208,7 +212,8 @@ __global__ void __launch_bounds__(256, 2) k_ozaki_gemm(OzGemmJob job, int* statu
     }
     if (tid == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(done, 1);
+        mbar_init(tfull, 1);
+        mbar_init(tempty, OZ_EPI_WARPS);
         *fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -217,75 +222,122 @@ __global__ void __launch_bounds__(256, 2) k_ozaki_gemm(OzGemmJob job, int* statu
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (tid == 32) {
-        // producer: one bulk copy for the 8 A planes of a K chunk, 8 for the B rows c0 .. c0+31
-        for (int kc = 0; kc < OZ_NKC; ++kc) {
-            const int s = kc & 1;
-            if (kc >= OZ_STAGES && !mbar_wait(&empty[s], ((kc >> 1) - 1) & 1)) { atomicOr(fail, 1); break; }
-            mbar_expect_tx(&full[s], OZ_STAGE_A + OZ_STAGE_B);
-            const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
-            bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, OZ_STAGE_A, &full[s]);
-            for (int p = 0; p < OZ_S; ++p)
-                bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
-                         sb + chunk + p * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
-        }
-    } else if (tid == 0) {
-        // MMA issuer: for each stage, the 36 digit products with p + q <= 7 into group g = p + q
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_N >> 3) << 17) |
-                               ((uint32_t)(128 >> 4) << 24);
-        for (int kc = 0; kc < OZ_NKC; ++kc) {
-            const int s = kc & 1;
-            if (!mbar_wait(&full[s], (kc >> 1) & 1)) { atomicOr(fail, 2); break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
-            for (int p = 0; p < OZ_S; ++p)
-                for (int q = 0; p + q < OZ_G; ++q) {
-                    const int g = p + q;
-                    const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
-                    mma_bf16(tmem + g * OZ_N, oz_desc(a0 + p * OZ_CHUNK), oz_desc(b0 + q * (OZ_N * OZ_KC * 2)), idesc, acc);
+    if (warp == 1) {
+        if (lane == 0) {
+            // producer: stages (task, kc) in order; stage s = it & 1 is reused every other step
+            long long it = 0;
+            for (long long t = blockIdx.x; t < ntasks && !*(volatile int*)fail; t += gridDim.x) {
+                const unsigned char *sa, *sb;
+                double* C;
+                int c0;
+                double mult;
+                job.task(t, sa, sb, C, c0, mult);
+                for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
+                    const int s = (int)(it % OZ_STAGES);
+                    if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1))) {
+                        atomicOr(fail, 1);
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], OZ_STAGE_A + OZ_STAGE_B);
+                    const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
+                    bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, OZ_STAGE_A, &full[s]);
+                    for (int p = 0; p < OZ_S; ++p)
+                        bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
+                                 sb + chunk + p * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
                 }
-            mma_commit(&empty[s]);
-        }
-        mma_commit(done);
-    }
-    __syncthreads();      // role loops are done issuing; *fail is visible to every thread
-    const bool ok = *fail == 0 && mbar_wait(done, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows), columns
-        // 16 (w / 4) .. +15 of each of the 8 group accumulators
-        const int r = (warp & 3) * 32 + lane;
-        const int cbase = (warp >> 2) * 16;
-        const int er = exp_a[r];
-        const bool negm = mult < 0.0;
-        const int em = ilogb(fabs(mult));            // |mult| is a power of two (1 or 1/2)
-        for (int cb = cbase; cb < cbase + 16; cb += 8) {
-            uint32_t v[OZ_G][8];
-#pragma unroll
-            for (int g = 0; g < OZ_G; ++g)
-                tmem_ld8x(tmem + ((uint32_t)((warp & 3) * 32) << 16) + g * OZ_N + cb, v[g]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                // exact group sums (|.| < 2^24) -> fixed point with unit 2^-46:
-                // sum_g acc_g 2^(-7(g+2)) = (sum_(g<4) acc_g 2^(32-7g) + floor(sum_(g>=4) acc_g 2^(49-7g) / 2^17)) 2^-46
-                long long hi = 0, lo = 0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
-#pragma unroll
-                for (int g = 4; g < OZ_G; ++g) lo += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (49 - 7 * g));
-                const long long fx = hi + (lo >> 17);
-                const int c = c0 + cb + j;
-                double y = scale_pow2((double)fx, er + exp_b[c] - 46 + em);
-                double* cp = C + r + (long long)c * 128;
-                *cp = negm ? *cp + y : *cp - y;
             }
         }
-    } else if (tid == 0) {
-        atomicOr(status, ST_TIMEOUT);
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // MMA issuer: per stage the 36 digit products with p + q <= 7 into group g = p + q
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_N >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+            long long it = 0, nt = 0;
+            for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
+                if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1))) { atomicOr(fail, 4); break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool bad = false;
+                for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
+                    const int s = (int)(it % OZ_STAGES);
+                    if (!mbar_wait(&full[s], (uint32_t)((it / OZ_STAGES) & 1))) { atomicOr(fail, 2); bad = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
+                    for (int p = 0; p < OZ_S; ++p)
+                        for (int q = 0; p + q < OZ_G; ++q) {
+                            const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
+                            mma_bf16(tmem + (p + q) * OZ_N, oz_desc(a0 + p * OZ_CHUNK),
+                                     oz_desc(b0 + q * (OZ_N * OZ_KC * 2)), idesc, acc);
+                        }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(tfull);
+                if (bad) break;
+            }
+        }
+    } else {
+        // epilogue warps 2..9: rows of TMEM lane quarter w % 4, columns 32 ((w - 2) / 4) .. +31
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;
+        const int chalf = ((warp - 2) >> 2) * 32;
+        long long nt = 0;
+        for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
+            const unsigned char *sa, *sb;
+            double* C;
+            int c0;
+            double mult;
+            job.task(t, sa, sb, C, c0, mult);
+            if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            long long fx[32];
+#pragma unroll
+            for (int cb = 0; cb < 32; cb += 8) {
+                uint32_t v[OZ_G][8];
+#pragma unroll
+                for (int g = 0; g < OZ_G; ++g)
+                    tmem_ld8x(tmem + ((uint32_t)(quarter * 32) << 16) + g * OZ_N + chalf + cb, v[g]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    // exact group sums (|.| < 2^24) -> fixed point with unit 2^-46
+                    long long hi = 0, lo = 0;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
+#pragma unroll
+                    for (int g = 4; g < OZ_G; ++g) lo += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (49 - 7 * g));
+                    fx[cb + j] = hi + (lo >> 17);
+                }
+            }
+            // accumulators are in registers: hand TMEM back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+            const int* __restrict__ exp_a = (const int*)(sa + OZ_TILE_BYTES);
+            const int* __restrict__ exp_b = (const int*)(sb + OZ_TILE_BYTES);
+            const int er = exp_a[r] - 46 + ilogb(fabs(mult));     // |mult| is a power of two
+            const bool assign = job.assign != 0;
+            const bool negm = mult < 0.0;
+            double* __restrict__ Cr = C + r + (long long)(c0 + chalf) * 128;
+            // C values are loaded 16 at a time before any is stored, so their latencies overlap
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {
+                double cv[16];
+                int eb[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    cv[j] = assign ? 0.0 : Cr[(long long)(h + j) * 128];
+                    eb[j] = exp_b[c0 + chalf + h + j];
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const double y = fx_to_double(negm ? -fx[h + j] : fx[h + j], er + eb[j]);
+                    Cr[(long long)(h + j) * 128] = cv[j] - y;
+                }
+            }
+        }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (*fail && tid == 0) atomicOr(status, ST_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_G * OZ_N));
     }
@@ -304,9 +356,17 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
                       const char* family) {
     if (ctas <= 0) return 0;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
     cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    const long long grid = ctas < (long long)sms ? ctas : (long long)sms;    // persistent: one CTA per SM
     L.begin(family);
-    k_ozaki_gemm<<<(unsigned)ctas, 256, OZ_SMEM, L.stream>>>(job, status);
+    k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(job, ctas, status);
     L.count();
     return L.end(flops, 0.0);
 }

@@ -337,8 +337,8 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
             unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * ozaki_tile_bytes();
             SliceJob sj{S, SLICE_PANEL, k, T};
             if ((rc = launch_ozaki_slice(L, g, sj, m, true, panel))) return rc;
-            OzGemmJob oj{OZ_POTRF_UPD, k, T, S, panel, panel, ozaki_tile_bytes(), 1.0};
-            if ((rc = launch_ozaki_gemm(L, oj, tasks * 4, fl, status, "ozaki_potrf_update"))) return rc;
+            OzGemmJob oj{OZ_POTRF_UPD, k, T, S, panel, panel, ozaki_tile_bytes(), 1.0, 0};
+            if ((rc = launch_ozaki_gemm(L, oj, tasks * 2, fl, status, "ozaki_potrf_update"))) return rc;
             continue;
         }
         GemmParams gp{GEMM_POTRF_UPD, k, T, S, nullptr, nullptr};
@@ -401,8 +401,8 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         }
         const double fix_fl = m * 2.0 * nb3;
         for (int q = 0; q < 2; ++q) {      // E_ik = C_ik - 1/2 L_ik B_kk
-            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5};
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 4, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, fix_fl, status, "ozaki_sygst_fix"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {
             SliceJob ej{M[q], SLICE_PANEL, k, T};
@@ -410,14 +410,14 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         }
         const long long tasks = (long long)m * (m + 1) / 2;
         for (int q = 0; q < 2; ++q) {      // M_ij -= L_ik E_jk^T + E_ik L_jk^T
-            OzGemmJob t1{OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0};
-            if ((rc = launch_ozaki_gemm(L, t1, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
-            OzGemmJob t2{OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0};
-            if ((rc = launch_ozaki_gemm(L, t2, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+            OzGemmJob t1{OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0, 0};
+            if ((rc = launch_ozaki_gemm(L, t1, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+            OzGemmJob t2{OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0, 0};
+            if ((rc = launch_ozaki_gemm(L, t2, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {      // P_ik = E_ik - 1/2 L_ik B_kk
-            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5};
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 4, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, fix_fl, status, "ozaki_sygst_fix"))) return rc;
         }
     }
     for (int m = 1; m < T; ++m) {
@@ -435,8 +435,8 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         }
         const long long tasks = (long long)below * m;
         for (int q = 0; q < 2; ++q) {      // M_(i,kk) -= L_(i,m) M_(m,kk)
-            OzGemmJob j{OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0};
-            if ((rc = launch_ozaki_gemm(L, j, tasks * 4, tasks * 2.0 * nb3, status, "ozaki_sygst_rowupd"))) return rc;
+            OzGemmJob j{OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0, 0};
+            if ((rc = launch_ozaki_gemm(L, j, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_rowupd"))) return rc;
         }
     }
     return rc;
