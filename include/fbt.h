@@ -167,6 +167,12 @@ long long fbt_launch_count(fbt_ctx* ctx, int reset);
  * reset), inputs and results included; either pointer may be NULL. */
 fbt_status fbt_transfer_bytes(fbt_ctx* ctx, long long* h2d, long long* d2h, int reset);
 
+/* Number of mle_eval calls that reused the Cholesky factor left by the previous evaluation at
+ * the same theta (the Fisher iteration at the point the line search accepted, Algorithm 1): the
+ * factor of Sigma(theta) is kept in the context after every successful evaluation, and an
+ * mle_eval at an identical theta generates only the partials instead of Sigma and its factor. */
+long long fbt_factor_reuses(fbt_ctx* ctx);
+
 /* Geometry of a context: padded size, tile size, tile count per side. */
 fbt_status fbt_geometry(fbt_ctx* ctx, long long* n, long long* n_pad, int* nb, int* tiles);
 

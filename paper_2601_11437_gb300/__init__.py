@@ -192,6 +192,10 @@ def fbt_profile_read(ctx: Context) -> dict:
                                        bytes=arr[i].bytes) for i in range(min(cnt.value, 64))}
 
 
+def fbt_factor_reuses(ctx: Context) -> int:
+    return int(_lib.load().fbt_factor_reuses(ctx.handle))
+
+
 def fbt_launch_count(ctx: Context, reset: bool = False) -> int:
     return int(_lib.load().fbt_launch_count(ctx.handle, int(bool(reset))))
 

@@ -50,6 +50,7 @@ SIGNATURES = {
     "fbt_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(FbtKernelStat), C.c_int, C.POINTER(C.c_int)]),
     "fbt_launch_count": (C.c_longlong, [C.c_void_p, C.c_int]),
+    "fbt_factor_reuses": (C.c_longlong, [C.c_void_p]),
     "fbt_transfer_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]),
     "fbt_geometry": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                C.POINTER(C.c_int), C.POINTER(C.c_int)]),

@@ -114,10 +114,19 @@ struct fbt_ctx {
     double *S = nullptr, *SA = nullptr, *SN = nullptr;
     unsigned char* slices = nullptr;         // digit planes of L (emulated-FP64 tile updates)
     unsigned char* slice_scratch = nullptr;  // digit planes of transform panels / rows
+    double* winv = nullptr;                  // inverses of the diagonal factor tiles
+    unsigned char* wsl = nullptr;            // their digit planes
+    double* yscratch = nullptr;              // two scratch tiles
     Profiler* prof = nullptr;
     long long launches = 0;
     long long h2d_bytes = 0, d2h_bytes = 0;
     EvalOut host_out{};
+    // The S slab holds the Cholesky factor of Sigma(factor_theta) after every successful
+    // evaluation; an Algorithm 3 evaluation at the same theta (the Fisher iteration at the point
+    // the line search just accepted) reuses it instead of regenerating and refactoring Sigma.
+    bool factor_valid = false;
+    double factor_theta[3] = {0.0, 0.0, 0.0};
+    long long factor_reuses = 0;
 };
 
 static thread_local std::string tl_cuda_error;
@@ -170,12 +179,19 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     // the two-sided transforms), plus scratch for two panels / rows and two diagonal tiles
     const bool emu = o.precision == FBT_PREC_FP64_EMULATED;
     const long long nL = T * (T - 1) / 2 > 0 ? T * (T - 1) / 2 : 1;
-    const long long nX = 2 * (T > 1 ? T - 1 : 1) + 2;
+    const long long nX = 2 * (T > 1 ? T - 1 : 1) + 6;
     char* psl = emu ? take((size_t)nL * ozaki_tile_bytes()) : nullptr;
-    char* psx = emu && o.with_derivatives ? take((size_t)nX * ozaki_tile_bytes()) : nullptr;
+    const bool ed = emu && o.with_derivatives;
+    char* psx = ed ? take((size_t)nX * ozaki_tile_bytes()) : nullptr;
+    char* pwi = ed ? take((size_t)T * nb * nb * sizeof(double)) : nullptr;       // W_k = L_kk^-1
+    char* pws = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // digit planes of W_k
+    char* pyy = ed ? take((size_t)2 * nb * nb * sizeof(double)) : nullptr;       // two scratch tiles
     if (base && c) {
         c->slices = (unsigned char*)psl;
         c->slice_scratch = (unsigned char*)psx;
+        c->winv = (double*)pwi;
+        c->wsl = (unsigned char*)pws;
+        c->yscratch = (double*)pyy;
         c->X = (double*)pX; c->Y = (double*)pY; c->Z = (double*)pZ;
         c->vy = (double*)pvy; c->vw = (double*)pvw;
         c->perm = (long long*)pperm; c->bbox = (double*)pbbox;
@@ -313,11 +329,18 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     const Geom& g = c->g;
     int rc = 0;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
+    const bool reuse = deriv && c->factor_valid && theta[0] == c->factor_theta[0] &&
+                       theta[1] == c->factor_theta[1] && theta[2] == c->factor_theta[2];
+    c->factor_valid = false;
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
-    if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN, deriv, c->status)))
+    if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, reuse ? nullptr : c->S, c->SA, c->SN, deriv,
+                              c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
-    if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices)))
+    if (reuse) {
+        c->factor_reuses += 1;
+    } else if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices))) {
         return cuda_fail((cudaError_t)rc, "potrf");
+    }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
     if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
     if (deriv) {
@@ -329,7 +352,8 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
         CK(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
            "clear slots");
         if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd, c->status,
-                               c->opts.precision, c->slices, c->slice_scratch)))
+                               c->opts.precision, c->slices, c->slice_scratch, c->winv, c->wsl,
+                               c->yscratch)))
             return cuda_fail((cudaError_t)rc, "sygst");
     }
     if ((rc = launch_assemble(L, g, c->vy, c->slots, deriv, c->tc, c->status, c->out)))
@@ -341,6 +365,8 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     if (c->host_out.status & ST_TIMEOUT) return FBT_ERR_TIMEOUT;
     if (c->host_out.status & ST_NOT_PD) return FBT_ERR_NOT_PD;
     if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
+    c->factor_valid = true;
+    for (int i = 0; i < 3; ++i) c->factor_theta[i] = theta[i];
     return FBT_OK;
 }
 
@@ -372,6 +398,7 @@ fbt_status fbt_generate(fbt_ctx* c, const double theta[3], int with_derivatives)
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     Launcher L = launcher(c);
     int rc;
+    c->factor_valid = false;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
     if ((rc = launch_generate(L, c->g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN,
@@ -440,6 +467,8 @@ fbt_status fbt_profile_read(fbt_ctx* c, fbt_kernel_stat* out, int cap, int* coun
     }
     return FBT_OK;
 }
+
+long long fbt_factor_reuses(fbt_ctx* c) { return c ? c->factor_reuses : -1; }
 
 fbt_status fbt_transfer_bytes(fbt_ctx* c, long long* h2d, long long* d2h, int reset) {
     if (!c) return FBT_ERR_ARG;

@@ -34,7 +34,9 @@ struct ThetaConsts {
     double jitter;
 };
 
+constexpr int EXP_TABLE = 64;
 struct QuadTables {
+    double exp2tab[EXP_TABLE];            // 2^(j/64), j = 0..63 (table of the exponential)
     double st2[QUAD_LEVELS][QUAD_NODES];  // 2 sinh^2(t_j / 2)  (x cosh t = x + x * st2)
     double wa[QUAD_LEVELS][QUAD_NODES];   // w_j cosh(nu t_j)
     double wb[QUAD_LEVELS][QUAD_NODES];   // w_j cosh((nu - 1) t_j)
@@ -81,19 +83,24 @@ __host__ __device__ inline long long strict_lower_pos(int i, int k, int T) {
 
 // Which tiles a slicing launch reads: block t of the launch slices tile (ti, tj) of src into
 // position t of the slice buffer.
-enum : int { SLICE_PANEL = 0, SLICE_ROW = 1, SLICE_DIAG = 2 };
+enum : int { SLICE_PANEL = 0, SLICE_ROW = 1, SLICE_DIAG = 2, SLICE_PTR = 3 };
 struct SliceJob {
     const double* src;
     int mode, k, T;
-    __device__ void tile(int t, int& ti, int& tj) const {
+    // tile t of the launch: (ti, tj) of the slab src; SLICE_PTR: tile t of a contiguous tile array
+    __device__ const double* tile_ptr(int t, int nb) const {
+        if (mode == SLICE_PTR) return src + (long long)t * nb * nb;
+        int ti, tj;
         if (mode == SLICE_PANEL) { ti = k + 1 + t; tj = k; }       // column k below the diagonal
         else if (mode == SLICE_ROW) { ti = k; tj = t; }            // row k left of the diagonal
         else { ti = k; tj = k; }                                    // diagonal tile k
+        return src + tile_offset(ti, tj, T, nb);
     }
 };
 
 // One task of an update launch: 128 rows x 64 columns of one target tile (two per tile).
-enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3 };
+enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3, OZ_SINGLE = 4,
+             OZ_ROWSOLVE = 5 };
 struct OzGemmJob {
     int mode, k, T;
     double* C;                     // target slab
@@ -117,11 +124,19 @@ struct OzGemmJob {
             Ct = C + tile_offset(k + 1 + (int)tsk, k, T, 128);
             sa = slA + (size_t)tsk * tile_bytes;
             sb = slB;
-        } else {                  // OZ_SYGST_ROWUPD, m = k: targets (i, kk), i > m > kk
+        } else if (mode == OZ_SYGST_ROWUPD) {   // m = k: targets (i, kk), i > m > kk
             const int kk = (int)(tsk % k), ii = (int)(tsk / k);
             Ct = C + tile_offset(k + 1 + ii, kk, T, 128);
             sa = slA + (size_t)ii * tile_bytes;
             sb = slB + (size_t)kk * tile_bytes;
+        } else if (mode == OZ_SINGLE) {         // one tile: C points at it
+            Ct = C;
+            sa = slA;
+            sb = slB;
+        } else {                                // OZ_ROWSOLVE, m = k: targets (m, kk), kk < m
+            Ct = C + tile_offset(k, (int)tsk, T, 128);
+            sa = slA;
+            sb = slB + (size_t)tsk * tile_bytes;
         }
     }
 };
@@ -176,10 +191,12 @@ int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, in
 // two-sided transform B = L^-1 M L^-T of both derivative slabs in place, with the trace and
 // Frobenius-product partials of the result
 // precision PREC_FP64_OZAKI: L_slices holds the digit planes of every strictly-lower tile of L
-// (written by launch_potrf), scratch room for 2 (T - 1) + 2 more sliced tiles
+// (written by launch_potrf); scratch: room for 2 (T - 1) + 6 more sliced tiles; Winv: T FP64 tiles
+// (inverses of the diagonal factor tiles), Wsl: their digit planes, Y: 2 FP64 scratch tiles
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                  double* diag_slots, double* offd_slots, int* status, int precision = PREC_FP64,
-                 const unsigned char* L_slices = nullptr, unsigned char* scratch = nullptr);
+                 const unsigned char* L_slices = nullptr, unsigned char* scratch = nullptr,
+                 double* Winv = nullptr, unsigned char* Wsl = nullptr, double* Y = nullptr);
 int strips_per_tile(int nb);
 
 // v <- L^-1 v (trans = false) or v <- L^-T v (trans = true), tile by tile

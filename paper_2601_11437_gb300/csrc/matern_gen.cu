@@ -41,9 +41,27 @@ __device__ double digamma_pos(double x) {
 
 __device__ inline double clamp_finite(double v) { return v > 1.0e308 ? 1.0e308 : v; }
 
+// e^a for a <= 0 by table-driven argument reduction (P. T. P. Tang, "Table-driven implementation
+// of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
+// a = (64 m + j) ln2/64 + r with |r| <= ln2/128, e^a = 2^m 2^(j/64) e^r, e^r - 1 by its degree-5
+// Taylor polynomial (truncation < 4e-17 relative), ln2/64 split into a 36-bit head (n * head is
+// exact for |n| < 2^17) and a tail, 2^m applied to the exponent field.  Error ~2 ulp.
+__device__ __forceinline__ double exp_nonpos(double a, const double* __restrict__ tab) {
+    if (a < -700.0) return 0.0;                                 // keeps 2^m y a normal number
+    const double n = rint(a * 92.33248261689366);               // 64 / ln 2
+    double r = fma(-n, 0x1.62e42fefa0000p-7, a);               // ln 2 / 64, head
+    r = fma(-n, 0x1.cf79abc9e3b3ap-46, r);                      // ln 2 / 64, tail
+    const int ni = (int)n;
+    const int j = ni & (EXP_TABLE - 1), m = ni >> 6;
+    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
+    const double y = fma(tab[j], p, tab[j]);                    // 2^(j/64) e^r in [1, 2)
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+}
+
 __global__ void k_prep_theta(double sigma2, double alpha, double nu, double jitter,
                              ThetaConsts* __restrict__ tc, QuadTables* __restrict__ qt) {
     const int j = threadIdx.x;
+    if (j < EXP_TABLE) qt->exp2tab[j] = exp2(j / (double)EXP_TABLE);
     for (int l = 0; l < QUAD_LEVELS; ++l) {
         const double h = c_level_h[l];
         const double t = j * h;
@@ -81,25 +99,32 @@ __device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& t
                                                   const double* __restrict__ st2,
                                                   const double* __restrict__ wa,
                                                   const double* __restrict__ wb,
-                                                  const double* __restrict__ wd) {
+                                                  const double* __restrict__ wd,
+                                                  const double* __restrict__ etab) {
     MaternVals v{0.0, 0.0, 0.0};
     if (x < X_ZERO_BELOW) { v.r = 1.0; return v; }
     if (x > X_UNDERFLOW) return v;
     int l = x <= c_level_xmax[0] ? 0 : x <= c_level_xmax[1] ? 1 : x <= c_level_xmax[2] ? 2 : 3;
     const int base = l * QUAD_NODES;
     double sa = 0.0, sb = 0.0, sd = 0.0;
-    for (int j = 0; j < QUAD_NODES; ++j) {
-        const double e = exp(-x * st2[base + j]);
-        const double ta = e * wa[base + j];
-        sa += ta;
-        bool done = ta <= STOP_REL * sa;
-        if (DERIV) {
-            const double tb = e * wb[base + j];
-            const double td = e * wd[base + j];
-            sb += tb;
-            sd += td;
-            done = done && tb <= STOP_REL * sb && td <= STOP_REL * sd;
+    // four nodes per round; the stopping test (last terms below STOP_REL of the sums, which
+    // can only happen past the integrand's peak) is evaluated once per round
+    for (int j = 0; j < QUAD_NODES; j += 4) {
+        double ta = 0.0, tb = 0.0, td = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double e = exp_nonpos(-x * st2[base + j + u], etab);
+            ta = e * wa[base + j + u];
+            sa += ta;
+            if (DERIV) {
+                tb = e * wb[base + j + u];
+                td = e * wd[base + j + u];
+                sb += tb;
+                sd += td;
+            }
         }
+        bool done = ta <= STOP_REL * sa;
+        if (DERIV) done = done && tb <= STOP_REL * sb && td <= STOP_REL * sd;
         if (done) break;
     }
     const double lx = log(x);
@@ -128,7 +153,9 @@ __global__ void __launch_bounds__(256) k_generate(Geom g, const double* __restri
     double* s_wb = sm + 2 * NTAB;
     double* s_wd = sm + 3 * NTAB;
     double* s_xy = sm + (DERIV ? 4 : 2) * NTAB;
+    double* s_etab = s_xy + 4 * g.nb;
     const int nb = g.nb, T = g.T;
+    for (int q = threadIdx.x; q < EXP_TABLE; q += blockDim.x) s_etab[q] = qt->exp2tab[q];
     for (int q = threadIdx.x; q < NTAB; q += blockDim.x) {
         s_st2[q] = (&qt->st2[0][0])[q];
         s_wa[q] = (&qt->wa[0][0])[q];
@@ -166,13 +193,13 @@ __global__ void __launch_bounds__(256) k_generate(Geom g, const double* __restri
             const double dx = s_xy[r] - s_xy[2 * nb + c];
             const double dy = s_xy[nb + r] - s_xy[3 * nb + c];
             const double x = sqrt(dx * dx + dy * dy) * tc.inv_alpha;
-            const MaternVals v = matern_corr<DERIV>(x, tc, s_st2, s_wa, s_wb, s_wd);
+            const MaternVals v = matern_corr<DERIV>(x, tc, s_st2, s_wa, s_wb, s_wd, s_etab);
             s = tc.sigma2 * v.r;
             sa = tc.sigma2 * v.da;
             sn = tc.sigma2 * v.dn;
         }
         bad |= !isfinite(s) || (DERIV && (!isfinite(sa) || !isfinite(sn)));
-        S[base + e] = s;
+        if (S) S[base + e] = s;            // S == nullptr: Sigma's factor is kept, partials only
         if (DERIV) {
             SA[base + e] = sa;
             SN[base + e] = sn;
@@ -185,7 +212,7 @@ int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y
                     const ThetaConsts* tc, const QuadTables* qt, double* S, double* SA,
                     double* SN, bool deriv, int* status) {
     const long long tiles = num_tiles(g.T);
-    const size_t smem = (size_t)((deriv ? 4 : 2) * QUAD_LEVELS * QUAD_NODES + 4 * g.nb) * sizeof(double);
+    const size_t smem = (size_t)((deriv ? 4 : 2) * QUAD_LEVELS * QUAD_NODES + 4 * g.nb + EXP_TABLE) * sizeof(double);
     const double entries = (double)tiles * g.nb * g.nb;
     L.begin(deriv ? "generate_deriv" : "generate");
     if (deriv) {

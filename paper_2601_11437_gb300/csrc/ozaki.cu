@@ -62,9 +62,7 @@ __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ 
     // u * 128 in FP64, without FP64 arithmetic.
     __shared__ int s_exp[32];
     const int t = blockIdx.x >> 2, rq = (blockIdx.x & 3) * 32;
-    int ti, tj;
-    job.tile(t, ti, tj);
-    const double* X = job.src + tile_offset(ti, tj, T, nb);
+    const double* X = job.tile_ptr(t, nb);
     unsigned char* out = dst + (size_t)t * (OZ_TILE_BYTES + 128 * sizeof(double));
     int* exp_out = (int*)(out + OZ_TILE_BYTES);
     if (threadIdx.x < 32) {
@@ -298,12 +296,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    // exact group sums (|.| < 2^24) -> fixed point with unit 2^-46
+                    // exact group sums -> fixed point with unit 2^-46.  |acc_g| < 2^22 for g <= 1
+                    // (at most 2 products of < 2^21), so adding 1.5 * 2^23 in FP32 leaves the
+                    // integer in the low mantissa bits exactly; g = 2..4 (|acc| < 2^24) convert
+                    // with F2I; g = 5..7 enter fx only after a right shift by at least 3 bits, so
+                    // the ulp-4 rounding of adding 1.5 * 2^25 moves fx by at most 1/4 unit.
                     long long hi = 0, lo = 0;
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
+                    for (int g = 0; g < 2; ++g) {
+                        const int iv = __float_as_int(__uint_as_float(v[g][j]) + 12582912.0f) - 0x4B400000;
+                        hi += (long long)iv * (1ll << (32 - 7 * g));
+                    }
 #pragma unroll
-                    for (int g = 4; g < OZ_G; ++g) lo += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (49 - 7 * g));
+                    for (int g = 2; g < 4; ++g)
+                        hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
+                    lo += (long long)__float2int_rn(__uint_as_float(v[4][j])) * (1ll << 21);
+#pragma unroll
+                    for (int g = 5; g < OZ_G; ++g) {
+                        const int iv = (__float_as_int(__uint_as_float(v[g][j]) + 50331648.0f) - 0x4C400000) * 4;
+                        lo += (long long)iv * (1ll << (49 - 7 * g));
+                    }
                     fx[cb + j] = hi + (lo >> 17);
                 }
             }

@@ -357,52 +357,142 @@ int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, in
     return cudaErrorInvalidValue;
 }
 
-// Two-sided transform with the GEMM-shaped updates on tensor cores (emulated FP64).
+// ------------------------------------------------------------------------------------------
+// Inverses of the diagonal factor tiles, W_k = L_kk^-1, all k at once (one CTA each), in place in
+// shared memory by the column-oriented algorithm: from the last column to the first,
+// W_jj = 1 / L_jj and W_(j+1:,j) = -W_jj * W_(j+1:,j+1:) L_(j+1:,j).
+// ------------------------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(256) k_trtri_all(const double* __restrict__ S, int T,
+                                                   double* __restrict__ W) {
+    extern __shared__ double A[];
+    constexpr int LD = NB + 1;
+    __shared__ double t[NB];
+    const int k = blockIdx.x;
+    const double* tile = S + tile_offset(k, k, T, NB);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        A[r + c * LD] = r >= c ? tile[e] : 0.0;
+    }
+    __syncthreads();
+    for (int j = NB - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) A[j + j * LD] = 1.0 / A[j + j * LD];
+        for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) t[i] = A[i + j * LD];
+        __syncthreads();
+        const double ajj = -A[j + j * LD];
+        for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) {
+            double acc = 0.0;
+            for (int q = j + 1; q <= i; ++q) acc = fma(A[i + q * LD], t[q], acc);
+            A[i + j * LD] = acc * ajj;
+        }
+        __syncthreads();
+    }
+    double* out = W + (long long)k * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        out[e] = r >= c ? A[r + c * LD] : 0.0;
+    }
+}
+
+// Trace and Frobenius-product partials of the final transformed tiles (one CTA per lower tile,
+// fixed-order reduction): diagonal tile k -> diag slots [k][strip 0] = (tr B0, tr B1, <B0,B0>,
+// <B0,B1>, <B1,B1>), off-diagonal tile -> offd slots [tile][strip 0] = (<B0,B0>, <B0,B1>, <B1,B1>);
+// the other strip slots are zeroed.
+__global__ void __launch_bounds__(256) k_frob_tiles(Geom g, const double* __restrict__ B0,
+                                                    const double* __restrict__ B1, int nstrips,
+                                                    double* __restrict__ diag_slots,
+                                                    double* __restrict__ offd_slots) {
+    __shared__ double red[5][256];
+    const int T = g.T, nb = g.nb;
+    const long long t = blockIdx.x;
+    int j = (int)(((2.0 * T + 1.0) - sqrt((2.0 * T + 1.0) * (2.0 * T + 1.0) - 8.0 * (double)t)) * 0.5);
+    if (j < 0) j = 0;
+    while (j > 0 && tile_index(j, j, T) > t) --j;
+    while (j + 1 < T && tile_index(j + 1, j + 1, T) <= t) ++j;
+    const int i = j + (int)(t - tile_index(j, j, T));
+    const long long base = t * (long long)nb * nb;
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const double x = B0[base + e], y = B1[base + e];
+        if (i == j && (e % nb) == (e / nb)) { a[0] += x; a[1] += y; }
+        a[2] = fma(x, x, a[2]);
+        a[3] = fma(x, y, a[3]);
+        a[4] = fma(y, y, a[4]);
+    }
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < nstrips) {
+        const bool first = threadIdx.x == 0;
+        if (i == j) {
+            double* o = diag_slots + ((long long)i * nstrips + threadIdx.x) * 5;
+            for (int q = 0; q < 5; ++q) o[q] = first ? red[q][0] : 0.0;
+        } else {
+            double* o = offd_slots + (t * nstrips + threadIdx.x) * 3;
+            for (int q = 0; q < 3; ++q) o[q] = first ? red[q + 2][0] : 0.0;
+        }
+    }
+}
+
+// Two-sided transform with every GEMM-shaped step on tensor cores (emulated FP64): the
+// triangular solves use the inverted diagonal factor tiles W_k, so they are tile products too.
 static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                        double* diag_slots, double* offd_slots, int* status,
-                       const unsigned char* LS, unsigned char* scratch) {
-    constexpr int NB = 128, NS = NB / STRIP;
+                       const unsigned char* LS, unsigned char* scratch, double* Winv,
+                       unsigned char* Wsl, double* Y) {
+    constexpr int NB = 128;
     const int T = g.T;
     const size_t tb = ozaki_tile_bytes();
-    const size_t smem2 = (size_t)2 * STRIP * (NB + 1) * sizeof(double);
-    cudaFuncSetAttribute(k_trsm_strip<NB, false, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     const double nb3 = (double)NB * NB * NB;
-    const double tbytes = 8.0 * NB * NB;
-    unsigned char* X0 = scratch;                                  // E panel / row of M0
-    unsigned char* X1 = scratch + (size_t)(T > 1 ? T - 1 : 1) * tb; // E panel / row of M1
-    unsigned char* D0 = scratch + (size_t)2 * (T > 1 ? T - 1 : 1) * tb;
-    unsigned char* D1 = D0 + tb;
+    const long long span = T > 1 ? T - 1 : 1;
+    unsigned char* Xs[2] = {scratch, scratch + (size_t)span * tb};       // panels / rows
+    unsigned char* Ds[2] = {scratch + (size_t)2 * span * tb, scratch + (size_t)(2 * span + 1) * tb};
+    unsigned char* Zs[2] = {scratch + (size_t)(2 * span + 2) * tb, scratch + (size_t)(2 * span + 3) * tb};
     double* M[2] = {M0, M1};
-    unsigned char* Xs[2] = {X0, X1};
-    unsigned char* Ds[2] = {D0, D1};
+    double* Ys[2] = {Y, Y + NB * NB};
     int rc = 0;
+    {
+        const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
+        cudaFuncSetAttribute(k_trtri_all<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        L.begin("trtri");
+        k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
+        L.count();
+        if ((rc = L.end(T * nb3 / 3.0, 16.0 * T * NB * NB))) return rc;
+        SliceJob wj{Winv, SLICE_PTR, 0, T};
+        if ((rc = launch_ozaki_slice(L, g, wj, T, true, Wsl))) return rc;
+    }
+    const double tile_fl = 2.0 * nb3;
     for (int k = 0; k < T; ++k) {
-        TrsmParams tp{TRSM_SYGST_DIAG_R, k, T, S, M0, M1, diag_slots};
-        L.begin("trsm_sygst");
-        k_trsm_strip<NB, false, 2, 0><<<NS, 256, smem2, L.stream>>>(tp);
-        L.count();
-        tp.mode = TRSM_SYGST_DIAG_L;
-        k_trsm_strip<NB, true, 2, 1><<<NS, 256, smem2, L.stream>>>(tp);
-        L.count();
-        if ((rc = L.end(4.0 * nb3, 6.0 * tbytes))) return rc;
-        const int m = T - k - 1;
-        if (m == 0) break;
-        tp.mode = TRSM_SYGST_PANEL;
-        L.begin("trsm_sygst");
-        k_trsm_strip<NB, false, 2, 0><<<m * NS, 256, smem2, L.stream>>>(tp);
-        L.count();
-        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tbytes))) return rc;
-        const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
+        const unsigned char* Wk = Wsl + (size_t)k * tb;
+        // B_kk = W_k M_kk W_k^T: Y = M_kk W_k^T, then B_kk = W_k Y
         for (int q = 0; q < 2; ++q) {
             SliceJob dj{M[q], SLICE_DIAG, k, T};
             if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
+            OzGemmJob y{OZ_SINGLE, k, T, Ys[q], Ds[q], Wk, tb, -1.0, 1};
+            if ((rc = launch_ozaki_gemm(L, y, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
+            SliceJob zj{Ys[q], SLICE_PTR, 0, T};
+            if ((rc = launch_ozaki_slice(L, g, zj, 1, false, Zs[q]))) return rc;
+            OzGemmJob b{OZ_SINGLE, k, T, M[q] + tile_offset(k, k, T, NB), Wk, Zs[q], tb, -1.0, 1};
+            if ((rc = launch_ozaki_gemm(L, b, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
         }
-        const double fix_fl = m * 2.0 * nb3;
+        const int m = T - k - 1;
+        if (m == 0) break;
+        const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
+        for (int q = 0; q < 2; ++q) {      // C_ik = M_ik W_k^T, then the digit planes of B_kk
+            SliceJob pj{M[q], SLICE_PANEL, k, T};
+            if ((rc = launch_ozaki_slice(L, g, pj, m, true, Xs[q]))) return rc;
+            OzGemmJob c{OZ_SYGST_FIX, k, T, M[q], Xs[q], Wk, tb, -1.0, 1};
+            if ((rc = launch_ozaki_gemm(L, c, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
+            SliceJob dj{M[q], SLICE_DIAG, k, T};
+            if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
+        }
         for (int q = 0; q < 2; ++q) {      // E_ik = C_ik - 1/2 L_ik B_kk
             OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {
             SliceJob ej{M[q], SLICE_PANEL, k, T};
@@ -411,21 +501,24 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         const long long tasks = (long long)m * (m + 1) / 2;
         for (int q = 0; q < 2; ++q) {      // M_ij -= L_ik E_jk^T + E_ik L_jk^T
             OzGemmJob t1{OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0, 0};
-            if ((rc = launch_ozaki_gemm(L, t1, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+            if ((rc = launch_ozaki_gemm(L, t1, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
             OzGemmJob t2{OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0, 0};
-            if ((rc = launch_ozaki_gemm(L, t2, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_update"))) return rc;
+            if ((rc = launch_ozaki_gemm(L, t2, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {      // P_ik = E_ik - 1/2 L_ik B_kk
             OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, fix_fl, status, "ozaki_sygst_fix"))) return rc;
+            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
         }
     }
+    // B_(m,kk) = W_m (P_(m,kk) - sum_(kk<p<m) L_mp B_(p,kk)), row by row
     for (int m = 1; m < T; ++m) {
-        TrsmParams tp{TRSM_SYGST_ROW, m, T, S, M0, M1, offd_slots};
-        L.begin("trsm_sygst");
-        k_trsm_strip<NB, true, 2, 2><<<m * NS, 256, smem2, L.stream>>>(tp);
-        L.count();
-        if ((rc = L.end(2.0 * m * nb3, 4.0 * m * tbytes))) return rc;
+        const unsigned char* Wm = Wsl + (size_t)m * tb;
+        for (int q = 0; q < 2; ++q) {
+            SliceJob rj{M[q], SLICE_ROW, m, T};
+            if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
+            OzGemmJob r{OZ_ROWSOLVE, m, T, M[q], Wm, Xs[q], tb, -1.0, 1};
+            if ((rc = launch_ozaki_gemm(L, r, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
+        }
         const int below = T - m - 1;
         if (below == 0) continue;
         const unsigned char* Lp = LS + strict_lower_pos(m + 1, m, T) * tb;
@@ -436,10 +529,13 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         const long long tasks = (long long)below * m;
         for (int q = 0; q < 2; ++q) {      // M_(i,kk) -= L_(i,m) M_(m,kk)
             OzGemmJob j{OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0, 0};
-            if ((rc = launch_ozaki_gemm(L, j, tasks * 2, tasks * 2.0 * nb3, status, "ozaki_sygst_rowupd"))) return rc;
+            if ((rc = launch_ozaki_gemm(L, j, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_rowupd"))) return rc;
         }
     }
-    return rc;
+    L.begin("frob_epilogue");
+    k_frob_tiles<<<(unsigned)num_tiles(T), 256, 0, L.stream>>>(g, M0, M1, strips_per_tile(NB), diag_slots, offd_slots);
+    L.count();
+    return L.end(6.0 * num_tiles(T) * NB * NB, 16.0 * num_tiles(T) * NB * NB);
 }
 
 template <int NB>
@@ -509,9 +605,11 @@ static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, d
 
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                  double* diag_slots, double* offd_slots, int* status, int precision,
-                 const unsigned char* L_slices, unsigned char* scratch) {
+                 const unsigned char* L_slices, unsigned char* scratch, double* Winv,
+                 unsigned char* Wsl, double* Y) {
     if (g.nb == 128 && precision == PREC_FP64_OZAKI)
-        return sygst_ozaki(L, g, S, M0, M1, diag_slots, offd_slots, status, L_slices, scratch);
+        return sygst_ozaki(L, g, S, M0, M1, diag_slots, offd_slots, status, L_slices, scratch, Winv,
+                           Wsl, Y);
     if (g.nb == 128) return sygst_impl<128>(L, g, S, M0, M1, diag_slots, offd_slots);
     if (g.nb == 64) return sygst_impl<64>(L, g, S, M0, M1, diag_slots, offd_slots);
     return cudaErrorInvalidValue;

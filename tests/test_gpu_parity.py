@@ -196,3 +196,25 @@ def test_shift_to_nelder_mead_and_final_fisher(monkeypatch):
     assert st.loglik == pytest.approx(ref.loglik, rel=1e-8)
     Iref = likelihood.loglik_score_fisher(locs, z, tuple(st.theta[:])).fisher
     assert rel_err(np.array(st.fisher[:]).reshape(3, 3), Iref) < TOL_EVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
+def test_factor_reuse_at_the_accepted_point_is_bitwise_identical(precision):
+    # Algorithm 1 evaluates l at the accepted point in the line search and then runs the Fisher
+    # iteration there: the second evaluation reuses the Cholesky factor of the first
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(300, 16, (1.0, 0.1, 0.9))
+    theta = (0.9, 0.08, 1.1)
+    a = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    b = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    ll_a = fbt.mle_loglik(a, theta)
+    ea = fbt.mle_eval(a, theta)
+    assert fbt.fbt_factor_reuses(a) == 1
+    eb = fbt.mle_eval(b, theta)
+    assert fbt.fbt_factor_reuses(b) == 0
+    assert ea[0] == eb[0] == ll_a
+    assert np.array_equal(ea[1], eb[1]) and np.array_equal(ea[2], eb[2])
+    # a different theta, or a generation in between, does not reuse
+    fbt.mle_loglik(a, (0.9, 0.08, 1.2))
+    fbt.mle_eval(a, theta)
+    assert fbt.fbt_factor_reuses(a) == 1
