@@ -57,12 +57,19 @@ typedef struct {
                           /* are permutation invariant, the reordering groups near locations     */
     int with_derivatives; /* 1 (default): workspace for mle_eval; 0: mle_loglik only             */
     int device;           /* CUDA device ordinal; default 0                                        */
-    int precision;        /* arithmetic of the tile updates: FBT_PREC_FP64 (default, FP64 DFMA)   */
-                          /* or FBT_PREC_FP64_EMULATED (FP64-accurate products on the BF16 tensor  */
-                          /* cores by 7-bit slicing; needs nb = 128)                              */
+    int precision;        /* arithmetic of the tile updates: FBT_PREC_FP64 (default, FP64 DFMA),  */
+                          /* FBT_PREC_FP64_EMULATED (FP64-accurate products on the BF16 tensor     */
+                          /* cores by 7-bit slicing) or FBT_PREC_MIXED (per tile product 8, 3 or 1 */
+                          /* digit planes, FP64 / FP32 / BF16-class, chosen from the operand tiles' */
+                          /* largest entries against mixed_tol); the last two need nb = 128.       */
+                          /* Diagonal-tile Cholesky, inverses, generation, solves of the field,   */
+                          /* the log-determinant and the final reductions stay FP64 throughout.   */
+    double mixed_tol;     /* FBT_PREC_MIXED: a tile product whose largest possible entry stays     */
+                          /* below mixed_tol * sigma^2 * 2^6 uses one plane, below 2^20 times that */
+                          /* three planes; default 1e-12                                           */
 } fbt_opts;
 
-enum { FBT_PREC_FP64 = 0, FBT_PREC_FP64_EMULATED = 1 };
+enum { FBT_PREC_FP64 = 0, FBT_PREC_FP64_EMULATED = 1, FBT_PREC_MIXED = 2 };
 
 void fbt_default_opts(fbt_opts* opts);
 

@@ -63,12 +63,12 @@ class Context:
             pass
 
 
-PREC_FP64, PREC_FP64_EMULATED = 0, 1
+PREC_FP64, PREC_FP64_EMULATED, PREC_MIXED = 0, 1, 2
 
 
 def fbt_create(locs, z, *, nb: int = 128, jitter: float = 1e-8, reorder: bool = True,
                with_derivatives: bool = True, device: int = 0, stream=None,
-               workspace: str = "torch", precision: int = PREC_FP64) -> Context:
+               workspace: str = "torch", precision: int = PREC_FP64, mixed_tol: float = 1e-12) -> Context:
     """fbt_create: locs (n, 2) and z (n,) as float64 numpy arrays (host) or CUDA tensors (device)."""
     import torch
     lib = _lib.load()
@@ -79,6 +79,7 @@ def fbt_create(locs, z, *, nb: int = 128, jitter: float = 1e-8, reorder: bool = 
     opts.nb, opts.jitter, opts.reorder = nb, jitter, int(bool(reorder))
     opts.with_derivatives, opts.device = int(bool(with_derivatives)), device
     opts.precision = int(precision)
+    opts.mixed_tol = float(mixed_tol)
 
     def ptr(a, shape):
         if isinstance(a, torch.Tensor):

@@ -12,7 +12,8 @@ c_double_p = C.POINTER(C.c_double)
 
 class FbtOpts(C.Structure):
     _fields_ = [("jitter", C.c_double), ("nb", C.c_int), ("reorder", C.c_int),
-                ("with_derivatives", C.c_int), ("device", C.c_int), ("precision", C.c_int)]
+                ("with_derivatives", C.c_int), ("device", C.c_int), ("precision", C.c_int),
+                ("mixed_tol", C.c_double)]
 
 
 class FbtBtOpts(C.Structure):

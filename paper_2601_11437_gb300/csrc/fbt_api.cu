@@ -177,7 +177,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pSN = o.with_derivatives ? take(slab) : nullptr;
     // emulated FP64: digit planes of every strictly-lower tile of L (kept from the Cholesky for
     // the two-sided transforms), plus scratch for two panels / rows and two diagonal tiles
-    const bool emu = o.precision == FBT_PREC_FP64_EMULATED;
+    const bool emu = o.precision == FBT_PREC_FP64_EMULATED || o.precision == FBT_PREC_MIXED;
     const long long nL = T * (T - 1) / 2 > 0 ? T * (T - 1) / 2 : 1;
     const long long nX = 2 * (T > 1 ? T - 1 : 1) + 6;
     char* psl = emu ? take((size_t)nL * ozaki_tile_bytes()) : nullptr;
@@ -206,7 +206,9 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
 
 static bool opts_valid(const fbt_opts& o) {
     return (o.nb == 64 || o.nb == 128) && o.jitter >= 0.0 && isfinite(o.jitter) && o.device >= 0 &&
-           (o.precision == FBT_PREC_FP64 || (o.precision == FBT_PREC_FP64_EMULATED && o.nb == 128));
+           (o.precision == FBT_PREC_FP64 ||
+            ((o.precision == FBT_PREC_FP64_EMULATED || o.precision == FBT_PREC_MIXED) && o.nb == 128)) &&
+           (o.precision != FBT_PREC_MIXED || (o.mixed_tol > 0.0 && o.mixed_tol < 1.0));
 }
 
 extern "C" {
@@ -219,6 +221,7 @@ void fbt_default_opts(fbt_opts* o) {
     o->with_derivatives = 1;
     o->device = 0;
     o->precision = FBT_PREC_FP64;
+    o->mixed_tol = 1e-12;
 }
 
 size_t fbt_workspace_bytes(long long n, const fbt_opts* opts) {
@@ -336,9 +339,18 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, reuse ? nullptr : c->S, c->SA, c->SN, deriv,
                               c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
+    MixedPolicy pol;
+    if (c->opts.precision == FBT_PREC_MIXED) {
+        // a tile product whose largest possible entry is below tol * sigma^2 * 2^6 may use one
+        // 7-bit digit plane, below tol * sigma^2 * 2^20 three planes (see MixedPolicy)
+        const double l2 = log2(c->opts.mixed_tol * theta[0]);
+        pol.on = 1;
+        pol.e_fp32 = (int)floor(l2) - 1;
+        pol.e_fp64 = (int)floor(l2) + 13;
+    }
     if (reuse) {
         c->factor_reuses += 1;
-    } else if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices))) {
+    } else if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol))) {
         return cuda_fail((cudaError_t)rc, "potrf");
     }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
@@ -353,7 +365,7 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
            "clear slots");
         if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd, c->status,
                                c->opts.precision, c->slices, c->slice_scratch, c->winv, c->wsl,
-                               c->yscratch)))
+                               c->yscratch, pol)))
             return cuda_fail((cudaError_t)rc, "sygst");
     }
     if ((rc = launch_assemble(L, g, c->vy, c->slots, deriv, c->tc, c->status, c->out)))

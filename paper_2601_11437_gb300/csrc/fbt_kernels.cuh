@@ -20,7 +20,16 @@ namespace fbt {
 enum : int { ST_NOT_PD = 1, ST_BESSEL = 2, ST_DOMAIN = 4, ST_TIMEOUT = 8 };
 
 // ---- arithmetic of the tile updates ----
-enum : int { PREC_FP64 = 0, PREC_FP64_OZAKI = 1 };
+enum : int { PREC_FP64 = 0, PREC_FP64_OZAKI = 1, PREC_MIXED = 2 };
+
+// Mixed path: a tile product with operand maxima 2^ea, 2^eb uses 8 digit planes (FP64-accurate)
+// if ea + eb >= e_fp64, 3 planes (21 bits, FP32-class) if ea + eb >= e_fp32, else 1 plane
+// (7 bits, BF16-class).  Thresholds come from the context's tau_fp64 / tau_fp32 relative to
+// sigma^2: e = ceil(log2(tau * sigma^2)) - 7 (the 7 accounts for the K = 128 terms).
+struct MixedPolicy {
+    int on = 0;
+    int e_fp64 = 0, e_fp32 = 0;
+};
 
 // ---- trapezoid quadrature of K_nu, K_{nu-1} and dK_nu/dnu (see matern_gen.cu) ----
 constexpr int QUAD_LEVELS = 4;
@@ -109,6 +118,8 @@ struct OzGemmJob {
     size_t tile_bytes;
     double mult;
     int assign;                    // 1: C = -mult * A B^T (overwrite); 0: C -= mult * A B^T
+    int mixed = 0;                 // 1: digit planes per task from the operand magnitudes
+    int e_fp64 = 0, e_fp32 = 0;    // exponent thresholds of the mixed path (see task_planes)
     __device__ void task(long long bid, const unsigned char*& sa, const unsigned char*& sb,
                          double*& Ct, int& c0, double& m) const {
         const long long tsk = bid >> 1;
@@ -187,7 +198,8 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
 // tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile;
 // precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`)
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
-                 int precision = PREC_FP64, unsigned char* slices = nullptr);
+                 int precision = PREC_FP64, unsigned char* slices = nullptr,
+                 const MixedPolicy& pol = MixedPolicy());
 // two-sided transform B = L^-1 M L^-T of both derivative slabs in place, with the trace and
 // Frobenius-product partials of the result
 // precision PREC_FP64_OZAKI: L_slices holds the digit planes of every strictly-lower tile of L
@@ -196,7 +208,8 @@ int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, in
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                  double* diag_slots, double* offd_slots, int* status, int precision = PREC_FP64,
                  const unsigned char* L_slices = nullptr, unsigned char* scratch = nullptr,
-                 double* Winv = nullptr, unsigned char* Wsl = nullptr, double* Y = nullptr);
+                 double* Winv = nullptr, unsigned char* Wsl = nullptr, double* Y = nullptr,
+                 const MixedPolicy& pol = MixedPolicy());
 int strips_per_tile(int nb);
 
 // v <- L^-1 v (trans = false) or v <- L^-T v (trans = true), tile by tile

@@ -77,6 +77,11 @@ __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ 
         const int e = E == 0 ? 0 : E - 1022;        // 2^(e-1) <= max |x| < 2^e (zero row: e = 0)
         s_exp[threadIdx.x] = e;
         exp_out[r] = e;
+        // largest exponent of a non-zero row among these 32 rows (-10000: all rows zero), for the
+        // per-task precision choice of the mixed path
+        int em = E == 0 ? -10000 : e;
+        for (int off = 16; off > 0; off >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, off));
+        if (threadIdx.x == 0) exp_out[128 + (rq >> 5)] = em;
     }
     __syncthreads();
     for (int w = threadIdx.x; w < 32 * 16; w += blockDim.x) {
@@ -190,6 +195,18 @@ __device__ inline double fx_to_double(long long fx, int s) {
 constexpr int OZ_THREADS = 320;
 constexpr int OZ_EPI_WARPS = 8;
 
+// Digit planes used for a task: 8 (FP64-accurate); in the mixed path 3 or 1 when the operand
+// tiles' largest entries, 2^ea and 2^eb, make the product small against the thresholds.
+__device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa, const unsigned char* sb) {
+    if (!job.mixed) return OZ_S;
+    const int* ha = (const int*)(sa + OZ_TILE_BYTES) + 128;
+    const int* hb = (const int*)(sb + OZ_TILE_BYTES) + 128;
+    const int ea = max(max(ha[0], ha[1]), max(ha[2], ha[3]));
+    const int eb = max(max(hb[0], hb[1]), max(hb[2], hb[3]));
+    const int e = ea + eb;
+    return e >= job.e_fp64 ? OZ_S : (e >= job.e_fp32 ? 3 : 1);
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, long long ntasks, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
     unsigned char* stA = oz_smem;                                    // [4][32 KB]
@@ -230,16 +247,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                 int c0;
                 double mult;
                 job.task(t, sa, sb, C, c0, mult);
+                const int np = task_planes(job, sa, sb);
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
                     if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1))) {
                         atomicOr(fail, 1);
                         break;
                     }
-                    mbar_expect_tx(&full[s], OZ_STAGE_A + OZ_STAGE_B);
+                    mbar_expect_tx(&full[s], (uint32_t)np * (OZ_CHUNK + OZ_N * OZ_KC * 2));
                     const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
-                    bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, OZ_STAGE_A, &full[s]);
-                    for (int p = 0; p < OZ_S; ++p)
+                    bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, (uint32_t)np * OZ_CHUNK, &full[s]);
+                    for (int p = 0; p < np; ++p)
                         bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
                                  sb + chunk + p * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
                 }
@@ -252,6 +270,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                                    ((uint32_t)(128 >> 4) << 24);
             long long it = 0, nt = 0;
             for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
+                const unsigned char *sa, *sb;
+                double* Cq;
+                int cq;
+                double mq;
+                job.task(t, sa, sb, Cq, cq, mq);
+                const int np = task_planes(job, sa, sb);
                 if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1))) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool bad = false;
@@ -260,8 +284,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                     if (!mbar_wait(&full[s], (uint32_t)((it / OZ_STAGES) & 1))) { atomicOr(fail, 2); bad = true; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
-                    for (int p = 0; p < OZ_S; ++p)
-                        for (int q = 0; p + q < OZ_G; ++q) {
+                    for (int p = 0; p < np; ++p)
+                        for (int q = 0; p + q < np; ++q) {
                             const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
                             mma_bf16(tmem + (p + q) * OZ_N, oz_desc(a0 + p * OZ_CHUNK),
                                      oz_desc(b0 + q * (OZ_N * OZ_KC * 2)), idesc, acc);
@@ -284,6 +308,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
             int c0;
             double mult;
             job.task(t, sa, sb, C, c0, mult);
+            const int np = task_planes(job, sa, sb);
             if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             long long fx[32];
@@ -294,6 +319,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                 for (int g = 0; g < OZ_G; ++g)
                     tmem_ld8x(tmem + ((uint32_t)(quarter * 32) << 16) + g * OZ_N + chalf + cb, v[g]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // groups this task did not accumulate hold an earlier task's data: count them as 0
+#pragma unroll
+                for (int g = 1; g < OZ_G; ++g)
+                    if (g >= np)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) v[g][j] = 0u;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     // exact group sums -> fixed point with unit 2^-46.  |acc_g| < 2^22 for g <= 1

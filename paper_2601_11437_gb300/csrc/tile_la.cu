@@ -305,9 +305,15 @@ __global__ void __launch_bounds__(256) k_gemm_tile(GemmParams p) {
 // ------------------------------------------------------------------------------------------
 // host orchestration
 // ------------------------------------------------------------------------------------------
+static inline OzGemmJob with_policy(OzGemmJob j, const MixedPolicy& pol) {
+    j.mixed = pol.on;
+    j.e_fp64 = pol.e_fp64;
+    j.e_fp32 = pol.e_fp32;
+    return j;
+}
 template <int NB>
 static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
-                      int precision, unsigned char* slices) {
+                      int precision, unsigned char* slices, const MixedPolicy& pol) {
     const int T = g.T;
     const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
     const size_t smem_trsm1 = (size_t)STRIP * (NB + 1) * sizeof(double);
@@ -332,12 +338,12 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
         const long long tasks = (long long)m * (m + 1) / 2;
         // algorithmic flops: 2 nb^3 per off-diagonal tile, nb^3 + nb^2 for a diagonal (SYRK) tile
         const double fl = (double)m * (m - 1) / 2 * 2.0 * nb3 + m * (nb3 + (double)NB * NB);
-        if (NB == 128 && precision == PREC_FP64_OZAKI) {
+        if (NB == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED)) {
             // digit planes of panel k, kept for the two-sided transforms
             unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * ozaki_tile_bytes();
             SliceJob sj{S, SLICE_PANEL, k, T};
             if ((rc = launch_ozaki_slice(L, g, sj, m, true, panel))) return rc;
-            OzGemmJob oj{OZ_POTRF_UPD, k, T, S, panel, panel, ozaki_tile_bytes(), 1.0, 0};
+            OzGemmJob oj = with_policy({OZ_POTRF_UPD, k, T, S, panel, panel, ozaki_tile_bytes(), 1.0, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, oj, tasks * 2, fl, status, "ozaki_potrf_update"))) return rc;
             continue;
         }
@@ -351,9 +357,9 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
 }
 
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
-                 int precision, unsigned char* slices) {
-    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices);
-    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices);
+                 int precision, unsigned char* slices, const MixedPolicy& pol) {
+    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices, pol);
+    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices, pol);
     return cudaErrorInvalidValue;
 }
 
@@ -443,7 +449,7 @@ __global__ void __launch_bounds__(256) k_frob_tiles(Geom g, const double* __rest
 static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                        double* diag_slots, double* offd_slots, int* status,
                        const unsigned char* LS, unsigned char* scratch, double* Winv,
-                       unsigned char* Wsl, double* Y) {
+                       unsigned char* Wsl, double* Y, const MixedPolicy& pol) {
     constexpr int NB = 128;
     const int T = g.T;
     const size_t tb = ozaki_tile_bytes();
@@ -472,11 +478,11 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         for (int q = 0; q < 2; ++q) {
             SliceJob dj{M[q], SLICE_DIAG, k, T};
             if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
-            OzGemmJob y{OZ_SINGLE, k, T, Ys[q], Ds[q], Wk, tb, -1.0, 1};
+            OzGemmJob y = with_policy({OZ_SINGLE, k, T, Ys[q], Ds[q], Wk, tb, -1.0, 1}, pol);
             if ((rc = launch_ozaki_gemm(L, y, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
             SliceJob zj{Ys[q], SLICE_PTR, 0, T};
             if ((rc = launch_ozaki_slice(L, g, zj, 1, false, Zs[q]))) return rc;
-            OzGemmJob b{OZ_SINGLE, k, T, M[q] + tile_offset(k, k, T, NB), Wk, Zs[q], tb, -1.0, 1};
+            OzGemmJob b = with_policy({OZ_SINGLE, k, T, M[q] + tile_offset(k, k, T, NB), Wk, Zs[q], tb, -1.0, 1}, pol);
             if ((rc = launch_ozaki_gemm(L, b, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
         }
         const int m = T - k - 1;
@@ -485,13 +491,13 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         for (int q = 0; q < 2; ++q) {      // C_ik = M_ik W_k^T, then the digit planes of B_kk
             SliceJob pj{M[q], SLICE_PANEL, k, T};
             if ((rc = launch_ozaki_slice(L, g, pj, m, true, Xs[q]))) return rc;
-            OzGemmJob c{OZ_SYGST_FIX, k, T, M[q], Xs[q], Wk, tb, -1.0, 1};
+            OzGemmJob c = with_policy({OZ_SYGST_FIX, k, T, M[q], Xs[q], Wk, tb, -1.0, 1}, pol);
             if ((rc = launch_ozaki_gemm(L, c, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
             SliceJob dj{M[q], SLICE_DIAG, k, T};
             if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
         }
         for (int q = 0; q < 2; ++q) {      // E_ik = C_ik - 1/2 L_ik B_kk
-            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
+            OzGemmJob j = with_policy({OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {
@@ -500,13 +506,13 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         }
         const long long tasks = (long long)m * (m + 1) / 2;
         for (int q = 0; q < 2; ++q) {      // M_ij -= L_ik E_jk^T + E_ik L_jk^T
-            OzGemmJob t1{OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0, 0};
+            OzGemmJob t1 = with_policy({OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, t1, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
-            OzGemmJob t2{OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0, 0};
+            OzGemmJob t2 = with_policy({OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, t2, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
         }
         for (int q = 0; q < 2; ++q) {      // P_ik = E_ik - 1/2 L_ik B_kk
-            OzGemmJob j{OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0};
+            OzGemmJob j = with_policy({OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
         }
     }
@@ -516,7 +522,7 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         for (int q = 0; q < 2; ++q) {
             SliceJob rj{M[q], SLICE_ROW, m, T};
             if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
-            OzGemmJob r{OZ_ROWSOLVE, m, T, M[q], Wm, Xs[q], tb, -1.0, 1};
+            OzGemmJob r = with_policy({OZ_ROWSOLVE, m, T, M[q], Wm, Xs[q], tb, -1.0, 1}, pol);
             if ((rc = launch_ozaki_gemm(L, r, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
         }
         const int below = T - m - 1;
@@ -528,7 +534,7 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         }
         const long long tasks = (long long)below * m;
         for (int q = 0; q < 2; ++q) {      // M_(i,kk) -= L_(i,m) M_(m,kk)
-            OzGemmJob j{OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0, 0};
+            OzGemmJob j = with_policy({OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0, 0}, pol);
             if ((rc = launch_ozaki_gemm(L, j, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_rowupd"))) return rc;
         }
     }
@@ -606,10 +612,10 @@ static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, d
 int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                  double* diag_slots, double* offd_slots, int* status, int precision,
                  const unsigned char* L_slices, unsigned char* scratch, double* Winv,
-                 unsigned char* Wsl, double* Y) {
-    if (g.nb == 128 && precision == PREC_FP64_OZAKI)
+                 unsigned char* Wsl, double* Y, const MixedPolicy& pol) {
+    if (g.nb == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED))
         return sygst_ozaki(L, g, S, M0, M1, diag_slots, offd_slots, status, L_slices, scratch, Winv,
-                           Wsl, Y);
+                           Wsl, Y, pol);
     if (g.nb == 128) return sygst_impl<128>(L, g, S, M0, M1, diag_slots, offd_slots);
     if (g.nb == 64) return sygst_impl<64>(L, g, S, M0, M1, diag_slots, offd_slots);
     return cudaErrorInvalidValue;

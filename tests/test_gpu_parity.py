@@ -218,3 +218,23 @@ def test_factor_reuse_at_the_accepted_point_is_bitwise_identical(precision):
     fbt.mle_loglik(a, (0.9, 0.08, 1.2))
     fbt.mle_eval(a, theta)
     assert fbt.fbt_factor_reuses(a) == 1
+
+
+def test_mixed_path_matches_oracle_at_default_tolerance_and_emulated_when_strict():
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(650, 4, (1.5, 0.07, 0.8))
+    theta = (1.2, 0.05, 0.63)
+    ref = likelihood.loglik_score_fisher(locs, z, theta)
+    mixed = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_MIXED)          # tol 1e-12
+    ll, g, I = fbt.mle_eval(mixed, theta)
+    assert ll == pytest.approx(ref.loglik, rel=1e-9)
+    assert rel_err(g, ref.score) < 1e-8 and rel_err(I, ref.fisher) < 1e-8
+    # a tolerance below every product's size keeps all 8 digit planes: the emulated-FP64 results
+    strict = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_MIXED, mixed_tol=1e-300)
+    emu = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_FP64_EMULATED)
+    a, b = fbt.mle_eval(strict, theta), fbt.mle_eval(emu, theta)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    # a loose tolerance drops planes and moves the result, within its bound
+    loose = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_MIXED, mixed_tol=1e-6)
+    c = fbt.mle_eval(loose, theta)
+    assert c[0] != b[0] and abs(c[0] - b[0]) < 1e-3 * abs(b[0])
