@@ -115,6 +115,18 @@ fbt_status mle_loglik(fbt_ctx* ctx, const double theta[3], double* loglik);
 fbt_status mle_eval(fbt_ctx* ctx, const double theta[3], double* loglik,
                     double score[3], double fisher[9]);
 
+/*
+ * l(theta) and its gradient by the adjoint (trace) form of Eq. 2,
+ *   dl/dtheta_i = 1/2 <w w^T - Sigma^-1, Sigma_i>_F,  w = Sigma^-1 z,
+ * with Sigma^-1 = L^-T L^-1 formed from the Cholesky factor and the partials Sigma_alpha,
+ * Sigma_nu regenerated entry by entry inside the reduction (never stored); dl/dsigma^2 by
+ * Algorithm 3, Step 2.  About n^3 flops against 7 n^3 / 3 for mle_eval, which also yields the
+ * Fisher information.  Requires with_derivatives, nb = 128 and precision
+ * FBT_PREC_FP64_EMULATED or FBT_PREC_MIXED (FBT_ERR_ARG otherwise).  Reuses the factor of a
+ * preceding evaluation at the same theta.
+ */
+fbt_status mle_loglik_grad(fbt_ctx* ctx, const double theta[3], double* loglik, double grad[3]);
+
 /* Options of the Fisher-BT driver (Algorithm 1, Sec. 2.1); fbt_default_bt_opts() fills the
  * paper's values: armijo_c 0.001, rho 0.5, slack 0.001, grad_tol 0.001, max_ll_calls 60,
  * max_grad_calls 20, nm_ftol 1e-9 (plus nm_max_calls 1000, max_halvings 64 as guards). */

@@ -16,9 +16,10 @@ class NotPositiveDefinite(ArithmeticError):
     """Raised when a Cholesky pivot is not strictly positive (or not finite)."""
 
 
-def cholesky(A: np.ndarray, nb: int = 64) -> np.ndarray:
-    """Lower-triangular L with A = L L^T, right-looking blocked algorithm."""
-    W = np.array(A, dtype=np.float64, copy=True)
+def cholesky(A: np.ndarray, nb: int = 64, overwrite: bool = False) -> np.ndarray:
+    """Lower-triangular L with A = L L^T, right-looking blocked algorithm (overwrite: factor A's
+    own storage in place, for matrices too large to copy)."""
+    W = A if overwrite else np.array(A, dtype=np.float64, copy=True)
     n = W.shape[0]
     for k0 in range(0, n, nb):
         k1 = min(n, k0 + nb)
@@ -32,6 +33,12 @@ def cholesky(A: np.ndarray, nb: int = 64) -> np.ndarray:
             W[k1:, j] = (W[k1:, j] - W[k1:, k0:j] @ W[j, k0:j]) / W[j, j]
         P = W[k1:, k0:k1]
         W[k1:, k1:] -= P @ P.T                       # trailing update
+    if overwrite:
+        for k0 in range(0, n, nb):                   # zero the strict upper triangle in blocks
+            k1 = min(n, k0 + nb)
+            W[k0:k1, k1:] = 0.0
+            W[k0:k1, k0:k1] = np.tril(W[k0:k1, k0:k1])
+        return W
     return np.tril(W)
 
 

@@ -32,10 +32,13 @@ def main(names):
         w = inputs.WORKLOADS[name]
         t0 = time.time()
         locs = w.locations()
-        z = fields.sample_field(locs, w.normals(), w.theta_true, jitter=w.jitter)
+        if w.n > 20000:
+            z = fields.sample_field_blocked(locs, w.normals(), w.theta_true, jitter=w.jitter)
+        else:
+            z = fields.sample_field(locs, w.normals(), w.theta_true, jitter=w.jitter)
         np.save(os.path.join(OUT, f"{name}_z.npy"), z.astype("<f8"))
         meta = dict(workload=name, n=w.n, seed=w.seed, theta_true=w.theta_true, jitter=w.jitter,
-                    locations_sha256=locations_sha256(locs), generator="oracle.fields.sample_field",
+                    locations_sha256=locations_sha256(locs), generator="oracle.fields.sample_field" + ("_blocked" if w.n > 20000 else ""),
                     command=f"python -m oracle.make_fields {name}", seconds=round(time.time() - t0, 1))
         with open(os.path.join(OUT, f"{name}_z.json"), "w") as f:
             json.dump(meta, f, indent=1)

@@ -140,6 +140,44 @@ def mle_eval(ctx: Context, theta):
     return ll.value, np.array(g[:]), np.array(I[:]).reshape(3, 3)
 
 
+def mle_loglik_grad(ctx: Context, theta):
+    """Adjoint: (l, grad l (3,)) through Sigma^-1 with the partials regenerated on the fly."""
+    ll, g = C.c_double(), (C.c_double * 3)()
+    st = _lib.load().mle_loglik_grad(ctx.handle, _dbl3(theta), C.byref(ll), g)
+    if st != FBT_OK:
+        raise FbtError(st, "mle_loglik_grad")
+    return ll.value, np.array(g[:])
+
+
+class MaternLogLik:
+    """torch.autograd.Function for l(theta): forward runs Algorithm 2 (mle_loglik), backward the
+    adjoint (mle_loglik_grad), which reuses the forward's Cholesky factor.  Use
+    MaternLogLik.apply(ctx, theta_tensor) with a float64 tensor of shape (3,)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, ctx: Context, theta):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, theta_t, handle_holder):
+                    th = [float(v) for v in theta_t.detach().cpu().tolist()]
+                    fctx.th = th
+                    fctx.holder = handle_holder
+                    return torch.tensor(mle_loglik(handle_holder, th), dtype=torch.float64)
+
+                @staticmethod
+                def backward(fctx, grad_out):
+                    _, g = mle_loglik_grad(fctx.holder, fctx.th)
+                    return grad_out * torch.tensor(g, dtype=torch.float64), None
+
+            cls._fn = _F
+        return cls._fn.apply(theta, ctx)
+
+
 def default_bt_opts() -> FbtBtOpts:
     bt = FbtBtOpts()
     _lib.load().fbt_default_bt_opts(C.byref(bt))

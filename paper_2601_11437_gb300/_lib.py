@@ -42,6 +42,7 @@ SIGNATURES = {
     "fbt_set_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "mle_loglik": (C.c_int, [C.c_void_p, c_double_p, c_double_p]),
     "mle_eval": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p, c_double_p]),
+    "mle_loglik_grad": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p]),
     "fbt_default_bt_opts": (None, [C.POINTER(FbtBtOpts)]),
     "fisher_bt_start": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p,
                                   C.POINTER(FbtBtOpts), C.POINTER(FbtState)]),

@@ -18,8 +18,8 @@ LIB = os.path.join(HERE, "libfbt.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["reorder.cu", "matern_gen.cu", "tile_la.cu", "vec_la.cu", "fbt_api.cu", "fisher_bt.cpp",
-           "fbt_noalloc.cu", "ozaki.cu"]
-HEADERS = [os.path.join(CSRC, "fbt_kernels.cuh"), os.path.join(INCLUDE, "fbt.h")]
+           "fbt_noalloc.cu", "ozaki.cu", "adjoint.cu"]
+HEADERS = [os.path.join(CSRC, "fbt_kernels.cuh"), os.path.join(CSRC, "fbt_matern.cuh"), os.path.join(INCLUDE, "fbt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

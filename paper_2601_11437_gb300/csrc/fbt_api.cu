@@ -116,6 +116,7 @@ struct fbt_ctx {
     unsigned char* slice_scratch = nullptr;  // digit planes of transform panels / rows
     double* winv = nullptr;                  // inverses of the diagonal factor tiles
     unsigned char* wsl = nullptr;            // their digit planes
+    unsigned char* wcs = nullptr;            // their digit planes, column-sliced
     double* yscratch = nullptr;              // two scratch tiles
     Profiler* prof = nullptr;
     long long launches = 0;
@@ -185,12 +186,14 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* psx = ed ? take((size_t)nX * ozaki_tile_bytes()) : nullptr;
     char* pwi = ed ? take((size_t)T * nb * nb * sizeof(double)) : nullptr;       // W_k = L_kk^-1
     char* pws = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // digit planes of W_k
+    char* pwc = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // W_k, column-sliced
     char* pyy = ed ? take((size_t)2 * nb * nb * sizeof(double)) : nullptr;       // two scratch tiles
     if (base && c) {
         c->slices = (unsigned char*)psl;
         c->slice_scratch = (unsigned char*)psx;
         c->winv = (double*)pwi;
         c->wsl = (unsigned char*)pws;
+        c->wcs = (unsigned char*)pwc;
         c->yscratch = (double*)pyy;
         c->X = (double*)pX; c->Y = (double*)pY; c->Z = (double*)pZ;
         c->vy = (double*)pvy; c->vw = (double*)pvw;
@@ -379,6 +382,75 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
     c->factor_valid = true;
     for (int i = 0; i < 3; ++i) c->factor_theta[i] = theta[i];
+    return FBT_OK;
+}
+
+// Adjoint pipeline: l and grad l through Sigma^-1 (no Fisher information, no stored partials).
+static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    Launcher L = launcher(c);
+    const Geom& g = c->g;
+    int rc = 0;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
+    const bool reuse = c->factor_valid && theta[0] == c->factor_theta[0] &&
+                       theta[1] == c->factor_theta[1] && theta[2] == c->factor_theta[2];
+    c->factor_valid = false;
+    MixedPolicy pol;
+    if (c->opts.precision == FBT_PREC_MIXED) {
+        const double l2 = log2(c->opts.mixed_tol * theta[0]);
+        pol.on = 1;
+        pol.e_fp32 = (int)floor(l2) - 1;
+        pol.e_fp64 = (int)floor(l2) + 13;
+    }
+    if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
+    if (reuse) {
+        c->factor_reuses += 1;
+    } else {
+        if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, nullptr, nullptr, false, c->status)))
+            return cuda_fail((cudaError_t)rc, "generate");
+        if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol)))
+            return cuda_fail((cudaError_t)rc, "potrf");
+    }
+    CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    CK(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+    if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
+    // Sigma^-1 into SN (W = L^-1 in SA on the way)
+    // all digit planes: the plane choice is scaled to Sigma's entries, not to its inverse's
+    if ((rc = launch_inverse_from_factor(L, g, c->S, c->SA, c->SN, c->status, c->slices, c->slice_scratch,
+                                         c->winv, c->wsl, c->wcs, MixedPolicy{})))
+        return cuda_fail((cudaError_t)rc, "inverse");
+    // the reduction's partials go to the quadratic-form slots; traces and Frobenius slots read 0,
+    // so the assembly's score_i = -tr/2 + q/2 is exactly the adjoint sum / 2
+    CK(cudaMemsetAsync(c->slots.diag, 0, (size_t)g.T * c->nstrips * 5 * sizeof(double), c->stream), "clear slots");
+    CK(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
+       "clear slots");
+    if ((rc = launch_adjoint_reduce(L, g, c->X, c->Y, c->SN, c->vw, c->tc, c->qt, c->slots.qform, c->status)))
+        return cuda_fail((cudaError_t)rc, "adjoint reduce");
+    if ((rc = launch_assemble(L, g, c->vy, c->slots, true, c->tc, c->status, c->out)))
+        return cuda_fail((cudaError_t)rc, "assemble");
+    CK(cudaMemcpyAsync(&c->host_out, c->out, sizeof(EvalOut), cudaMemcpyDeviceToHost, c->stream), "copy result");
+    c->d2h_bytes += (long long)sizeof(EvalOut);
+    CK(cudaStreamSynchronize(c->stream), "adjoint sync");
+    if (c->prof) c->prof->flush();
+    if (c->host_out.status & ST_TIMEOUT) return FBT_ERR_TIMEOUT;
+    if (c->host_out.status & ST_NOT_PD) return FBT_ERR_NOT_PD;
+    if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
+    c->factor_valid = true;
+    for (int i = 0; i < 3; ++i) c->factor_theta[i] = theta[i];
+    return FBT_OK;
+}
+
+fbt_status mle_loglik_grad(fbt_ctx* c, const double theta[3], double* loglik, double grad[3]) {
+    if (!c || !theta || !loglik || !grad) return FBT_ERR_ARG;
+    if (!c->opts.with_derivatives || c->g.nb != 128 ||
+        (c->opts.precision != FBT_PREC_FP64_EMULATED && c->opts.precision != FBT_PREC_MIXED))
+        return FBT_ERR_ARG;
+    if (!theta_ok(theta)) { *loglik = -INFINITY; return FBT_ERR_DOMAIN; }
+    fbt_status st = evaluate_adjoint(c, theta);
+    if (st != FBT_OK) { *loglik = -INFINITY; return st; }
+    *loglik = c->host_out.loglik;
+    for (int i = 0; i < 3; ++i) grad[i] = c->host_out.score[i];
     return FBT_OK;
 }
 

@@ -109,7 +109,7 @@ struct SliceJob {
 
 // One task of an update launch: 128 rows x 64 columns of one target tile (two per tile).
 enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3, OZ_SINGLE = 4,
-             OZ_ROWSOLVE = 5 };
+             OZ_ROWSOLVE = 5, OZ_LAUUM = 6 };
 struct OzGemmJob {
     int mode, k, T;
     double* C;                     // target slab
@@ -140,6 +140,12 @@ struct OzGemmJob {
             Ct = C + tile_offset(k + 1 + ii, kk, T, 128);
             sa = slA + (size_t)ii * tile_bytes;
             sb = slB + (size_t)kk * tile_bytes;
+        } else if (mode == OZ_LAUUM) {          // targets (i, j), j <= i <= p = k, from row p
+            int ii, jj;
+            tri_decode(tsk, ii, jj);
+            Ct = C + tile_offset(ii, jj, T, 128);
+            sa = slA + (size_t)ii * tile_bytes;
+            sb = slA + (size_t)jj * tile_bytes;
         } else if (mode == OZ_SINGLE) {         // one tile: C points at it
             Ct = C;
             sa = slA;
@@ -211,6 +217,20 @@ int launch_sygst(Launcher& L, const Geom& g, const double* S, double* M0, double
                  double* Winv = nullptr, unsigned char* Wsl = nullptr, double* Y = nullptr,
                  const MixedPolicy& pol = MixedPolicy());
 int strips_per_tile(int nb);
+
+// Sigma^-1 = L^-T L^-1 from the factor in S (emulated FP64 on tensor cores): W = L^-1 into the W
+// slab (tile forward substitution with the inverted diagonal tiles), then X = W^T W (lower tiles)
+// into the X slab.  Needs the digit planes of L (L_slices), scratch for 2 (T - 1) + 6 sliced
+// tiles, Winv (T FP64 tiles), Wsl and Wcs (T sliced tiles each).
+int launch_inverse_from_factor(Launcher& L, const Geom& g, const double* S, double* W, double* X,
+                               int* status, const unsigned char* L_slices, unsigned char* scratch,
+                               double* Winv, unsigned char* Wsl, unsigned char* Wcs,
+                               const MixedPolicy& pol);
+// per-tile partials f sum_(r,c) (w_r w_c - X_rc) dSigma/dtheta_i (r,c) for i = alpha, nu with the
+// partials regenerated on the fly (f = 2 off the diagonal): slots[2 t + i - 1]
+int launch_adjoint_reduce(Launcher& L, const Geom& g, const double* Xs, const double* Yc,
+                          const double* X, const double* w, const ThetaConsts* tc,
+                          const QuadTables* qt, double* slots, int* status);
 
 // v <- L^-1 v (trans = false) or v <- L^-T v (trans = true), tile by tile
 int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans);

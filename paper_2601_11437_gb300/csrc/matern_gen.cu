@@ -18,45 +18,11 @@
 #include <math.h>
 
 #include "fbt_kernels.cuh"
+#include "fbt_matern.cuh"
 
 namespace fbt {
 
-__constant__ double c_level_h[QUAD_LEVELS] = {0.15, 0.075, 0.0375, 0.01875};
-__constant__ double c_level_xmax[QUAD_LEVELS] = {20.0, 80.0, 320.0, 1280.0};
-constexpr double X_ZERO_BELOW = 2.5e-15;   // x smaller than this: coincident points, R = 1
-constexpr double X_UNDERFLOW = 720.0;      // x larger than this: R and partials underflow to 0
-constexpr double STOP_REL = 1e-17;
-
-// psi(x) for x > 0: recurrence psi(x) = psi(x + 1) - 1/x up to x >= 10, then the asymptotic
-// series ln x - 1/(2x) - sum_k B_2k / (2k x^2k) with B_2 .. B_14 (DLMF 5.11.2).
-__device__ double digamma_pos(double x) {
-    double acc = 0.0;
-    while (x < 10.0) { acc -= 1.0 / x; x += 1.0; }
-    const double b[7] = {1.0 / 6.0, -1.0 / 30.0, 1.0 / 42.0, -1.0 / 30.0, 5.0 / 66.0,
-                         -691.0 / 2730.0, 7.0 / 6.0};
-    double inv2 = 1.0 / (x * x), p = inv2, s = 0.0;
-    for (int k = 0; k < 7; ++k) { s += b[k] / (2.0 * (k + 1)) * p; p *= inv2; }
-    return acc + log(x) - 0.5 / x - s;
-}
-
 __device__ inline double clamp_finite(double v) { return v > 1.0e308 ? 1.0e308 : v; }
-
-// e^a for a <= 0 by table-driven argument reduction (P. T. P. Tang, "Table-driven implementation
-// of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
-// a = (64 m + j) ln2/64 + r with |r| <= ln2/128, e^a = 2^m 2^(j/64) e^r, e^r - 1 by its degree-5
-// Taylor polynomial (truncation < 4e-17 relative), ln2/64 split into a 36-bit head (n * head is
-// exact for |n| < 2^17) and a tail, 2^m applied to the exponent field.  Error ~2 ulp.
-__device__ __forceinline__ double exp_nonpos(double a, const double* __restrict__ tab) {
-    if (a < -700.0) return 0.0;                                 // keeps 2^m y a normal number
-    const double n = rint(a * 92.33248261689366);               // 64 / ln 2
-    double r = fma(-n, 0x1.62e42fefa0000p-7, a);               // ln 2 / 64, head
-    r = fma(-n, 0x1.cf79abc9e3b3ap-46, r);                      // ln 2 / 64, tail
-    const int ni = (int)n;
-    const int j = ni & (EXP_TABLE - 1), m = ni >> 6;
-    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
-    const double y = fma(tab[j], p, tab[j]);                    // 2^(j/64) e^r in [1, 2)
-    return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
-}
 
 __global__ void k_prep_theta(double sigma2, double alpha, double nu, double jitter,
                              ThetaConsts* __restrict__ tc, QuadTables* __restrict__ qt) {
@@ -89,52 +55,6 @@ int launch_prep_theta(Launcher& L, const double theta[3], double jitter, ThetaCo
     k_prep_theta<<<1, QUAD_NODES, 0, L.stream>>>(theta[0], theta[1], theta[2], jitter, tc, qt);
     L.count();
     return L.end(0.0, 0.0);
-}
-
-struct MaternVals { double r, da, dn; };
-
-// R(x), dR/dalpha, dR/dnu for x > 0 with tables in shared memory.
-template <bool DERIV>
-__device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& tc,
-                                                  const double* __restrict__ st2,
-                                                  const double* __restrict__ wa,
-                                                  const double* __restrict__ wb,
-                                                  const double* __restrict__ wd,
-                                                  const double* __restrict__ etab) {
-    MaternVals v{0.0, 0.0, 0.0};
-    if (x < X_ZERO_BELOW) { v.r = 1.0; return v; }
-    if (x > X_UNDERFLOW) return v;
-    int l = x <= c_level_xmax[0] ? 0 : x <= c_level_xmax[1] ? 1 : x <= c_level_xmax[2] ? 2 : 3;
-    const int base = l * QUAD_NODES;
-    double sa = 0.0, sb = 0.0, sd = 0.0;
-    // four nodes per round; the stopping test (last terms below STOP_REL of the sums, which
-    // can only happen past the integrand's peak) is evaluated once per round
-    for (int j = 0; j < QUAD_NODES; j += 4) {
-        double ta = 0.0, tb = 0.0, td = 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const double e = exp_nonpos(-x * st2[base + j + u], etab);
-            ta = e * wa[base + j + u];
-            sa += ta;
-            if (DERIV) {
-                tb = e * wb[base + j + u];
-                td = e * wd[base + j + u];
-                sb += tb;
-                sd += td;
-            }
-        }
-        bool done = ta <= STOP_REL * sa;
-        if (DERIV) done = done && tb <= STOP_REL * sb && td <= STOP_REL * sd;
-        if (done) break;
-    }
-    const double lx = log(x);
-    const double P = tc.norm * exp(tc.nu * lx - x);      // x^nu e^-x / (2^(nu-1) Gamma(nu))
-    v.r = P * sa;
-    if (DERIV) {
-        v.da = P * x * sb * tc.inv_alpha;
-        v.dn = P * ((lx - tc.c_nu) * sa + sd);
-    }
-    return v;
 }
 
 // One block per lower tile (column-major tile order), the whole nb x nb tile (diagonal tiles

@@ -544,6 +544,70 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
     return L.end(6.0 * num_tiles(T) * NB * NB, 16.0 * num_tiles(T) * NB * NB);
 }
 
+__global__ void k_copy_diag_tiles(const double* __restrict__ Winv, int T, int nb, double* __restrict__ W) {
+    const int k = blockIdx.x;
+    const double* src = Winv + (long long)k * nb * nb;
+    double* dst = W + tile_offset(k, k, T, nb);
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) dst[e] = src[e];
+}
+
+int launch_inverse_from_factor(Launcher& L, const Geom& g, const double* S, double* W, double* X,
+                               int* status, const unsigned char* LS, unsigned char* scratch,
+                               double* Winv, unsigned char* Wsl, unsigned char* Wcs,
+                               const MixedPolicy& pol) {
+    constexpr int NB = 128;
+    if (g.nb != NB) return cudaErrorInvalidValue;
+    const int T = g.T;
+    const size_t tb = ozaki_tile_bytes();
+    const double nb3 = (double)NB * NB * NB, tile_fl = 2.0 * nb3;
+    unsigned char* Xs = scratch;                                   // up to T sliced tiles
+    int rc = 0;
+    const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_trtri_all<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    L.begin("trtri");
+    k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
+    L.count();
+    if ((rc = L.end(T * nb3 / 3.0, 16.0 * T * NB * NB))) return rc;
+    SliceJob wr{Winv, SLICE_PTR, 0, T};
+    if ((rc = launch_ozaki_slice(L, g, wr, T, true, Wsl))) return rc;
+    if ((rc = launch_ozaki_slice(L, g, wr, T, false, Wcs))) return rc;
+    // W: diagonal tiles W_kk; below them A_ik = -L_ik W_kk, then row by row
+    // W_mk = W_mm A_mk and A_ik -= L_im W_mk (i > m) -- the forward substitution L W = I
+    L.begin("copy_tiles");
+    k_copy_diag_tiles<<<T, 256, 0, L.stream>>>(Winv, T, NB, W);
+    L.count();
+    if ((rc = L.end(0.0, 16.0 * T * NB * NB))) return rc;
+    for (int k = 0; k + 1 < T; ++k) {
+        const int m = T - k - 1;
+        const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
+        OzGemmJob a = with_policy({OZ_SYGST_FIX, k, T, W, Lp, Wcs + (size_t)k * tb, tb, 1.0, 1}, pol);
+        if ((rc = launch_ozaki_gemm(L, a, (long long)m * 2, m * tile_fl, status, "ozaki_trtri"))) return rc;
+    }
+    for (int m = 1; m < T; ++m) {
+        SliceJob rj{W, SLICE_ROW, m, T};
+        if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs))) return rc;
+        OzGemmJob r = with_policy({OZ_ROWSOLVE, m, T, W, Wsl + (size_t)m * tb, Xs, tb, -1.0, 1}, pol);
+        if ((rc = launch_ozaki_gemm(L, r, (long long)m * 2, m * tile_fl, status, "ozaki_trtri"))) return rc;
+        const int below = T - m - 1;
+        if (below == 0) continue;
+        if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs))) return rc;
+        const unsigned char* Lp = LS + strict_lower_pos(m + 1, m, T) * tb;
+        OzGemmJob u = with_policy({OZ_SYGST_ROWUPD, m, T, W, Lp, Xs, tb, 1.0, 0}, pol);
+        if ((rc = launch_ozaki_gemm(L, u, (long long)below * m * 2, below * m * tile_fl, status, "ozaki_trtri"))) return rc;
+    }
+    // X = W^T W: row p of W contributes W_pi^T W_pj to every (i, j), j <= i <= p
+    const size_t slab = (size_t)num_tiles(T) * NB * NB * sizeof(double);
+    if (cudaMemsetAsync(X, 0, slab, L.stream) != cudaSuccess) return cudaGetLastError();
+    for (int p = 0; p < T; ++p) {
+        SliceJob rj{W, SLICE_ROW, p, T};
+        if ((rc = launch_ozaki_slice(L, g, rj, p + 1, false, Xs))) return rc;
+        const long long tasks = (long long)(p + 1) * (p + 2) / 2;
+        OzGemmJob l = with_policy({OZ_LAUUM, p, T, X, Xs, Xs, tb, -1.0, 0}, pol);
+        if ((rc = launch_ozaki_gemm(L, l, tasks * 2, tasks * tile_fl, status, "ozaki_lauum"))) return rc;
+    }
+    return rc;
+}
+
 template <int NB>
 static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, double* M1,
                       double* diag_slots, double* offd_slots) {
