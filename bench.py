@@ -329,6 +329,137 @@ def run_native(args):
     return 0
 
 
+def load_batch(name: str):
+    """The stored batched-fields workload: per-field recipe, locations and z."""
+    meta = json.load(open(os.path.join(FIELDS, f"{name}_z.json")))
+    fl = inputs.batched_fields(meta["fields"])
+    zall = np.load(os.path.join(FIELDS, f"{name}_z.npy"))
+    h, out, o = hashlib.sha256(), [], 0
+    for f in fl:
+        locs = inputs.uniform_locations(f.n, f.seed)
+        h.update(np.ascontiguousarray(locs, dtype="<f8").tobytes())
+        out.append((f, locs, zall[o:o + f.n]))
+        o += f.n
+    if h.hexdigest() != meta["locations_sha256"] or o != zall.size:
+        raise RuntimeError(f"stored batch {name} does not belong to these locations")
+    return out
+
+
+def run_batch(args):
+    """Batched independent fields: a step is one Fisher-BT iteration of every field, all fields
+    driven concurrently (host thread pool, one stream per thread), each from its theta^(0) state."""
+    import torch
+    import paper_2601_11437_gb300 as fbt
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    batch = load_batch(args.workload)
+    prec = PRECISIONS[args.precision]
+    ctxs = [fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=prec) for _, locs, z in batch]
+    theta0s = np.array([f.theta0 for f, _, _ in batch])
+    st0, status = fbt.fisher_bt_start_batch(ctxs, theta0s, nthreads=args.threads)
+    running = [q for q in range(len(ctxs)) if st0[q].state == fbt.RUNNING]
+    run_ctxs = [ctxs[q] for q in running]
+    ns = np.array([batch[q][0].n for q in running], dtype=np.float64)
+
+    def one_step():
+        st = (fbt.FbtState * len(running))()
+        for i, q in enumerate(running):
+            ctypes.memmove(ctypes.byref(st[i]), ctypes.byref(st0[q]), ctypes.sizeof(fbt.FbtState))
+        fbt.fisher_bt_step_batch(run_ctxs, st, nthreads=args.threads)
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+    for c in run_ctxs:
+        fbt.fbt_launch_count(c, reset=True)
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    flops = 0.0
+    for _ in range(args.steps):
+        st = one_step()
+        for i, q in enumerate(running):
+            lls = st[i].n_ll - st0[q].n_ll - (st[i].n_grad - st0[q].n_grad)
+            flops += lls * ns[i] ** 3 / 3 + (st[i].n_grad - st0[q].n_grad) * 7 * ns[i] ** 3 / 3
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ck = clocks.stop()
+    launches = sum(fbt.fbt_launch_count(c) for c in run_ctxs)
+    for c in ctxs:
+        fbt.fbt_destroy(c)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "fields x Fisher-BT iterations/s (batched fields)", "value": len(running) * args.steps / sec,
+        "unit": "field-iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "fields": len(batch), "fields_stepped": len(running),
+                   "n_range": [int(ns.min()), int(ns.max())], "sum_n3": float((ns ** 3).sum()),
+                   "precision": args.precision, "threads": args.threads, "nb": args.nb,
+                   "timing": "host wall clock around each batched call (it synchronises every stream)"},
+        "aggregate_tflops_fp64_equivalent": flops / sec / 1e12,
+        "gpu_launches": launches, "clocks": ck, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """Adjoint gradient at theta_true: forward l (Algorithm 2), backward (adjoint), the Fisher path's
+    score and central finite differences of l, on one large field."""
+    import torch
+    import paper_2601_11437_gb300 as fbt
+    w, locs, z = load_field(args.workload)
+    ctx = fbt.fbt_create(locs, z, nb=128, precision=PRECISIONS[args.precision])
+    th = np.array(w.theta_true)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        fbt.mle_loglik(ctx, th * 1.01)
+        fbt.mle_loglik_grad(ctx, th * 1.01)
+    fwd, bwd = [], []
+    for _ in range(args.steps):
+        fbt.mle_loglik(ctx, th * 1.02)                    # a different point: the next forward factorises
+        ev[0].record(stream)
+        ll = fbt.mle_loglik(ctx, th)
+        ev[1].record(stream)
+        ll_g, g = fbt.mle_loglik_grad(ctx, th)            # reuses the forward's factor
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[1].elapsed_time(ev[2]))
+    ev[0].record(stream)
+    ll_e, g_e, _ = fbt.mle_eval(ctx, th)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    eval_ms = ev[0].elapsed_time(ev[1])
+    fd = np.empty(3)
+    for i in range(3):
+        h = 1e-6 * th[i]
+        tp, tm = th.copy(), th.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd[i] = (fbt.mle_loglik(ctx, tp) - fbt.mle_loglik(ctx, tm)) / (2 * h)
+    fbt.fbt_destroy(ctx)
+    n = w.n
+    line = {
+        "metric": "adjoint backward time (s)", "value": statistics.median(bwd) / 1e3, "unit": "s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": n, "theta": w.theta_true, "precision": args.precision},
+        "forward_s": statistics.median(fwd) / 1e3, "mle_eval_s": eval_ms / 1e3,
+        "backward_tflops_fp64_equivalent": (2 * n ** 3 / 3) / (statistics.median(bwd) * 1e-3) / 1e12,
+        "loglik": ll, "grad": g.tolist(), "score_fisher_path": g_e.tolist(), "grad_central_fd": fd.tolist(),
+        "rel_err_vs_fisher_path": float(np.abs(g - g_e).max() / np.abs(g_e).max()),
+        "rel_err_vs_fd": float(np.abs(g - fd).max() / np.abs(g).max()),
+        "loglik_equal": bool(ll == ll_g == ll_e),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +473,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-n", type=int, default=1536)
+    ap.add_argument("--threads", type=int, default=16, help="host threads of the batched workload")
+    ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
     args = ap.parse_args()
+    if args.workload.startswith("batch") and args.impl == "native":
+        return run_batch(args)
+    if args.adjoint:
+        return run_adjoint(args)
     if args.warmup < 3 and args.impl == "native" and not os.environ.get("FBT_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     return run_reference(args) if args.impl == "reference" else run_native(args)

@@ -166,6 +166,35 @@ fbt_status fisher_bt_step(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts* bt);
 fbt_status fisher_bt_run(fbt_ctx* ctx, const double* theta0, const double* theta_lo,
                          const double* theta_hi, const fbt_bt_opts* bt, fbt_state* out);
 
+/*
+ * Many independent fields (one context each, same device; a context may appear once).  A pool
+ * of nthreads host threads (<= 0: FBT_BATCH_DEFAULT_THREADS) drives the fields, largest first,
+ * each thread on its own CUDA stream, ordered after and before each context's own stream, so
+ * that the fields' kernels overlap on the GPU.  Nothing is exchanged between fields.  Every
+ * call returns when all fields are done: FBT_OK, or the first hard error (CUDA, OOM, TIMEOUT,
+ * ARG, STATE) of any field; the per-field statuses are in status[] either way.
+ */
+#define FBT_BATCH_DEFAULT_THREADS 16
+enum { FBT_BATCH_LOGLIK = 0, FBT_BATCH_EVAL = 1 };
+
+/* k candidates per field: thetas[(f k + j) 3 + d]; with FBT_BATCH_EVAL, out[(f k + j) 13 + ...]
+ * = (l, score[3], fisher[9]) as mle_eval, else out[f k + j] = l as mle_loglik; status[f k + j]
+ * is that evaluation's status. */
+fbt_status mle_eval_batch(fbt_ctx* const* ctxs, int nfields, const double* thetas, int k, int flags,
+                          double* out, int* status, int nthreads);
+
+/* fisher_bt_start / fisher_bt_step / fisher_bt_run per field (theta0s, theta_lo, theta_hi: 3 per
+ * field, or NULL as in fisher_bt_start); fisher_bt_step_batch leaves fields whose state is not
+ * FBT_RUNNING untouched (status FBT_OK). */
+fbt_status fisher_bt_start_batch(fbt_ctx* const* ctxs, int nfields, const double* theta0s,
+                                 const double* theta_lo, const double* theta_hi, const fbt_bt_opts* bt,
+                                 fbt_state* states, int* status, int nthreads);
+fbt_status fisher_bt_step_batch(fbt_ctx* const* ctxs, int nfields, fbt_state* states,
+                                const fbt_bt_opts* bt, int* status, int nthreads);
+fbt_status fisher_bt_run_batch(fbt_ctx* const* ctxs, int nfields, const double* theta0s,
+                               const double* theta_lo, const double* theta_hi, const fbt_bt_opts* bt,
+                               fbt_state* states, int* status, int nthreads);
+
 /* Per-kernel statistics, recorded with CUDA events on the context's stream while enabled. */
 typedef struct {
     const char* name;     /* kernel family                                                    */

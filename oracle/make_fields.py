@@ -6,6 +6,7 @@ oracle's own Matern covariance and textbook Cholesky (fields.sample_field) and s
 checksum of the locations it belongs to.
 
     python -m oracle.make_fields n16384
+    python -m oracle.make_fields batch2048      (the batched-fields workload, 2048 fields)
 """
 import hashlib
 import json
@@ -24,11 +25,34 @@ def locations_sha256(locs: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(locs, dtype="<f8").tobytes()).hexdigest()
 
 
+def write_batch(inputs, count: int, name: str):
+    """The batched-fields workload: every field's z, concatenated in field order, with the
+    per-field offsets and a checksum of all locations."""
+    t0 = time.time()
+    fl = inputs.batched_fields(count)
+    zs, h = [], hashlib.sha256()
+    for f in fl:
+        locs = inputs.uniform_locations(f.n, f.seed)
+        h.update(np.ascontiguousarray(locs, dtype="<f8").tobytes())
+        zs.append(fields.sample_field(locs, inputs.standard_normal(f.n, f.seed), f.theta_true))
+    offsets = np.concatenate([[0], np.cumsum([f.n for f in fl])]).tolist()
+    np.save(os.path.join(OUT, f"{name}_z.npy"), np.concatenate(zs).astype("<f8"))
+    meta = dict(workload=name, fields=count, offsets_end=offsets[-1], locations_sha256=h.hexdigest(),
+                recipe="paper_2601_11437_gb300.inputs.batched_fields", generator="oracle.fields.sample_field",
+                command=f"python -m oracle.make_fields {name}", seconds=round(time.time() - t0, 1))
+    with open(os.path.join(OUT, f"{name}_z.json"), "w") as fh:
+        json.dump(meta, fh, indent=1)
+    print(meta)
+
+
 def main(names):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from paper_2601_11437_gb300 import inputs
     os.makedirs(OUT, exist_ok=True)
     for name in names:
+        if name.startswith("batch"):
+            write_batch(inputs, int(name[len("batch"):]), name)
+            continue
         w = inputs.WORKLOADS[name]
         t0 = time.time()
         locs = w.locations()

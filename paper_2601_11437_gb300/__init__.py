@@ -211,6 +211,83 @@ def fisher_bt_run(ctx: Context, theta0=None, theta_lo=None, theta_hi=None, bt=No
     return st
 
 
+FBT_BATCH_LOGLIK, FBT_BATCH_EVAL = 0, 1
+
+
+def _handles(ctxs):
+    return (C.c_void_p * len(ctxs))(*[c.handle.value for c in ctxs])
+
+
+def _rows3(v, rows):
+    """(pointer, owner) of a contiguous (rows, 3) float64 copy of v, or (None, None)."""
+    if v is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(rows, 3))
+    return a.ctypes.data_as(_lib.c_double_p), a
+
+
+def mle_eval_batch(ctxs, thetas, *, full: bool = True, nthreads: int = 0):
+    """k candidates for each of F fields (thetas: (F, k, 3)).  full: returns (l (F, k),
+    score (F, k, 3), fisher (F, k, 3, 3), status (F, k)); else (l (F, k), status (F, k))."""
+    F = len(ctxs)
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(F, -1, 3))
+    k = th.shape[1]
+    stride = 13 if full else 1
+    out = np.zeros((F, k, stride))
+    status = np.zeros((F, k), dtype=np.int32)
+    s = _lib.load().mle_eval_batch(_handles(ctxs), F, th.ctypes.data_as(_lib.c_double_p), k,
+                                   FBT_BATCH_EVAL if full else FBT_BATCH_LOGLIK,
+                                   out.ctypes.data_as(_lib.c_double_p),
+                                   status.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+    if s != FBT_OK:
+        raise FbtError(s, "mle_eval_batch")
+    if full:
+        return out[..., 0], out[..., 1:4], out[..., 4:13].reshape(F, k, 3, 3), status
+    return out[..., 0], status
+
+
+def _batch_states(F):
+    return (FbtState * F)(), np.zeros(F, dtype=np.int32)
+
+
+def fisher_bt_start_batch(ctxs, theta0s=None, theta_lo=None, theta_hi=None, bt=None, nthreads: int = 0):
+    """fisher_bt_start per field; returns (states (FbtState array), status (F,))."""
+    F = len(ctxs)
+    states, status = _batch_states(F)
+    (p0, a0), (pl, al), (ph, ah) = _rows3(theta0s, F), _rows3(theta_lo, F), _rows3(theta_hi, F)
+    bt = bt or default_bt_opts()
+    s = _lib.load().fisher_bt_start_batch(_handles(ctxs), F, p0, pl, ph, C.byref(bt), states,
+                                          status.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+    if s != FBT_OK:
+        raise FbtError(s, "fisher_bt_start_batch")
+    return states, status
+
+
+def fisher_bt_step_batch(ctxs, states, bt=None, nthreads: int = 0):
+    """One Fisher-BT step of every field still running (in place); returns status (F,)."""
+    F = len(ctxs)
+    status = np.zeros(F, dtype=np.int32)
+    bt = bt or default_bt_opts()
+    s = _lib.load().fisher_bt_step_batch(_handles(ctxs), F, states, C.byref(bt),
+                                         status.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+    if s != FBT_OK:
+        raise FbtError(s, "fisher_bt_step_batch")
+    return status
+
+
+def fisher_bt_run_batch(ctxs, theta0s=None, theta_lo=None, theta_hi=None, bt=None, nthreads: int = 0):
+    """Algorithm 1 end to end for every field; returns (states, status (F,))."""
+    F = len(ctxs)
+    states, status = _batch_states(F)
+    (p0, a0), (pl, al), (ph, ah) = _rows3(theta0s, F), _rows3(theta_lo, F), _rows3(theta_hi, F)
+    bt = bt or default_bt_opts()
+    s = _lib.load().fisher_bt_run_batch(_handles(ctxs), F, p0, pl, ph, C.byref(bt), states,
+                                        status.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+    if s != FBT_OK:
+        raise FbtError(s, "fisher_bt_run_batch")
+    return states, status
+
+
 def fbt_destroy(ctx: Context) -> None:
     if ctx.handle and ctx.handle.value:
         _lib.load().fbt_destroy(ctx.handle)

@@ -49,6 +49,14 @@ SIGNATURES = {
     "fisher_bt_step": (C.c_int, [C.c_void_p, C.POINTER(FbtState), C.POINTER(FbtBtOpts)]),
     "fisher_bt_run": (C.c_int, [C.c_void_p, c_double_p, c_double_p, c_double_p,
                                 C.POINTER(FbtBtOpts), C.POINTER(FbtState)]),
+    "mle_eval_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, C.c_int, C.c_int, c_double_p,
+                                 C.POINTER(C.c_int), C.c_int]),
+    "fisher_bt_start_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, c_double_p, c_double_p,
+                                        C.POINTER(FbtBtOpts), C.POINTER(FbtState), C.POINTER(C.c_int), C.c_int]),
+    "fisher_bt_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(FbtState),
+                                       C.POINTER(FbtBtOpts), C.POINTER(C.c_int), C.c_int]),
+    "fisher_bt_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, c_double_p, c_double_p,
+                                      C.POINTER(FbtBtOpts), C.POINTER(FbtState), C.POINTER(C.c_int), C.c_int]),
     "fbt_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(FbtKernelStat), C.c_int, C.POINTER(C.c_int)]),
     "fbt_launch_count": (C.c_longlong, [C.c_void_p, C.c_int]),

@@ -18,10 +18,11 @@ LIB = os.path.join(HERE, "libfbt.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["reorder.cu", "matern_gen.cu", "tile_la.cu", "vec_la.cu", "fbt_api.cu", "fisher_bt.cpp",
-           "fbt_noalloc.cu", "ozaki.cu", "adjoint.cu"]
-HEADERS = [os.path.join(CSRC, "fbt_kernels.cuh"), os.path.join(CSRC, "fbt_matern.cuh"), os.path.join(INCLUDE, "fbt.h")]
+           "fbt_noalloc.cu", "ozaki.cu", "adjoint.cu", "fbt_batch.cpp"]
+HEADERS = [os.path.join(CSRC, h) for h in ("fbt_kernels.cuh", "fbt_matern.cuh", "fbt_ctx_access.h")] + \
+          [os.path.join(INCLUDE, "fbt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I", INCLUDE]
 
 
 def nvcc() -> str:
@@ -63,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     print(f"--- {os.path.basename(src)}\n{log}", file=sys.stderr)
     objs = [os.path.join(OBJDIR, s + ".o") for s in SOURCES]
     if force or jobs or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", LIB] + objs
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

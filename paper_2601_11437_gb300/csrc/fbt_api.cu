@@ -9,6 +9,7 @@
 
 #include "../../include/fbt.h"
 #include "fbt_kernels.cuh"
+#include "fbt_ctx_access.h"
 
 using namespace fbt;
 
@@ -596,3 +597,13 @@ const char* fbt_strerror(int s) {
 const char* fbt_last_cuda_error(void) { return tl_cuda_error.c_str(); }
 
 }  // extern "C"
+
+namespace fbt {
+cudaStream_t ctx_swap_stream(fbt_ctx* c, cudaStream_t s) {
+    cudaStream_t prev = c->stream;
+    c->stream = s;
+    return prev;
+}
+int ctx_device(const fbt_ctx* c) { return c->device; }
+long long ctx_n(const fbt_ctx* c) { return c->g.n; }
+}  // namespace fbt

@@ -399,13 +399,12 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
                       const char* family) {
     if (ctas <= 0) return 0;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {          // initialised once, also when several host threads launch
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 152;
+    }();
     cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
     const long long grid = ctas < (long long)sms ? ctas : (long long)sms;    // persistent: one CTA per SM
     L.begin(family);
