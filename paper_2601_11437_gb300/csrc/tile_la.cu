@@ -51,13 +51,12 @@ __global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int 
         __syncthreads();
         for (int r = j + 1 + threadIdx.x; r < NB; r += blockDim.x) A[r + j * LD] *= s_inv;
         __syncthreads();
-        const int m = NB - j - 1;
-        for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
-            const int rr = q % m, cc = q / m;
-            if (rr >= cc) {
-                const int r = j + 1 + rr, c = j + 1 + cc;
-                A[r + c * LD] -= A[r + j * LD] * A[c + j * LD];
-            }
+        // trailing update of the lower triangle: warp w takes columns j + 1 + w, + nwarps, ...,
+        // its lanes the rows c, c + 1, ... of each (no index division, no idle upper half)
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int c = j + 1 + warp; c < NB; c += nw) {
+            const double lc = A[c + j * LD];
+            for (int r = c + lane; r < NB; r += 32) A[r + c * LD] -= A[r + j * LD] * lc;
         }
         __syncthreads();
     }
@@ -65,10 +64,16 @@ __global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int 
         const int r = e % NB, c = e / NB;
         tile[e] = r >= c ? A[r + c * LD] : 0.0;
     }
+    // sum of log L_jj: one logarithm per thread, then a fixed-order tree
+    __shared__ double s_log[NB];
+    for (int j = threadIdx.x; j < NB; j += blockDim.x) s_log[j] = log(A[j + j * LD]);
+    __syncthreads();
+    for (int w = NB / 2; w > 0; w >>= 1) {
+        for (int j = threadIdx.x; j < w; j += blockDim.x) s_log[j] += s_log[j + w];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int j = 0; j < NB; ++j) s += log(A[j + j * LD]);
-        logdet_slots[k] = s;
+        logdet_slots[k] = s_log[0];
         if (s_bad) atomicOr(status, ST_NOT_PD);
     }
 }

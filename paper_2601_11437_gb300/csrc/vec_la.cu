@@ -14,31 +14,61 @@ namespace fbt {
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S, int T, int nb,
                                                    int m, double* __restrict__ v) {
-    extern __shared__ double sv[];
+    // the tile's lower triangle is staged in shared memory (leading dimension nb + 1: column and
+    // row walks are both free of bank conflicts), then one warp runs the substitution with the
+    // vector in registers, lane l holding entries l, l + 32, l + 64, l + 96: no block barrier
+    // inside the sequential loop
+    extern __shared__ double A[];
+    const int LD = nb + 1;
     const double* __restrict__ Lt = S + tile_offset(m, m, T, nb);
-    double* vm = v + (long long)m * nb;
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e % nb, c = e / nb;
+        if (r >= c) A[r + c * LD] = Lt[e];
+    }
     __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double* vm = v + (long long)m * nb;
+    const int nblk = nb / 32;
+    double x[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) x[s] = s < nblk ? vm[lane + 32 * s] : 0.0;
     if (!TRANS) {
-        for (int d = 0; d < nb; ++d) {
-            const double x = sv[d] / Lt[d + (long long)d * nb];
-            __syncthreads();
-            if (threadIdx.x == 0) sv[d] = x;
-            for (int dp = d + 1 + threadIdx.x; dp < nb; dp += blockDim.x)
-                sv[dp] -= Lt[dp + (long long)d * nb] * x;
-            __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (s >= nblk) break;
+            for (int dd = 0; dd < 32; ++dd) {
+                const int d = 32 * s + dd;
+                double xd = 0.0;
+                if (lane == dd) { xd = x[s] / A[d + d * LD]; x[s] = xd; }
+                xd = __shfl_sync(0xffffffffu, xd, dd);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int r = lane + 32 * t;
+                    if (t >= s && t < nblk && r > d) x[t] -= A[r + d * LD] * xd;
+                }
+            }
         }
     } else {
-        for (int d = nb - 1; d >= 0; --d) {
-            const double x = sv[d] / Lt[d + (long long)d * nb];
-            __syncthreads();
-            if (threadIdx.x == 0) sv[d] = x;
-            const double* __restrict__ Lrow = Lt + d;     // L[d][dp] = Lt[d + dp * nb], dp < d
-            for (int dp = threadIdx.x; dp < d; dp += blockDim.x) sv[dp] -= Lrow[(long long)dp * nb] * x;
-            __syncthreads();
+#pragma unroll
+        for (int s = 3; s >= 0; --s) {
+            if (s >= nblk) continue;
+            for (int dd = 31; dd >= 0; --dd) {
+                const int d = 32 * s + dd;
+                double xd = 0.0;
+                if (lane == dd) { xd = x[s] / A[d + d * LD]; x[s] = xd; }
+                xd = __shfl_sync(0xffffffffu, xd, dd);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int r = lane + 32 * t;
+                    if (t <= s && r < d) x[t] -= A[d + r * LD] * xd;     // L[d][r], r < d
+                }
+            }
         }
     }
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) vm[d] = sv[d];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (s < nblk) vm[lane + 32 * s] = x[s];
 }
 
 // forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i, thread per row)
@@ -76,12 +106,15 @@ __global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ 
 int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans) {
     const int T = g.T, nb = g.nb;
     const size_t smem = (size_t)nb * sizeof(double);
+    const size_t smem_diag = (size_t)nb * (nb + 1) * sizeof(double);
+    cudaFuncSetAttribute(k_trsv_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
+    cudaFuncSetAttribute(k_trsv_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     const double tb = 8.0 * nb * nb;
     int rc = 0;
     L.begin(trans ? "trsv_backward" : "trsv_forward");
     if (!trans) {
         for (int m = 0; m < T; ++m) {
-            k_trsv_diag<false><<<1, 256, smem, L.stream>>>(S, T, nb, m, v);
+            k_trsv_diag<false><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m + 1 < T) {
                 k_trsv_update<false><<<T - m - 1, 256, smem, L.stream>>>(S, T, nb, m, v);
@@ -90,7 +123,7 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
         }
     } else {
         for (int m = T - 1; m >= 0; --m) {
-            k_trsv_diag<true><<<1, 256, smem, L.stream>>>(S, T, nb, m, v);
+            k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m > 0) {
                 k_trsv_update<true><<<m, 256, smem, L.stream>>>(S, T, nb, m, v);
