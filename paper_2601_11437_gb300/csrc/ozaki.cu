@@ -265,9 +265,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
         }
     } else if (warp == 0) {
         if (lane == 0) {
-            // MMA issuer: per stage the 36 digit products with p + q <= 7 into group g = p + q
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_N >> 3) << 17) |
-                                   ((uint32_t)(128 >> 4) << 24);
+            // MMA issuer: per stage the 36 digit products with p + q <= 7 into group g = p + q.
+            // The groups occupy consecutive 64-column ranges of TMEM and the B planes consecutive
+            // 64-row blocks of the stage, so the products (p, q0 .. q1) are one MMA with
+            // N = 64 (q1 - q0 + 1) <= 256 into the columns of groups p + q0 .. p + q1: 12 MMAs
+            // per stage instead of 36, and A_p is read from shared memory once per MMA.
+            const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
             long long it = 0, nt = 0;
             for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
                 const unsigned char *sa, *sb;
@@ -285,10 +288,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
                     for (int p = 0; p < np; ++p)
-                        for (int q = 0; p + q < np; ++q) {
+                        for (int q0 = 0; p + q0 < np; q0 += 4) {
+                            const int nq = min(4, np - p - q0);
                             const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
-                            mma_bf16(tmem + (p + q) * OZ_N, oz_desc(a0 + p * OZ_CHUNK),
-                                     oz_desc(b0 + q * (OZ_N * OZ_KC * 2)), idesc, acc);
+                            const uint32_t idesc = idesc0 | ((uint32_t)(nq * OZ_N >> 3) << 17);
+                            mma_bf16(tmem + (p + q0) * OZ_N, oz_desc(a0 + p * OZ_CHUNK),
+                                     oz_desc(b0 + q0 * (OZ_N * OZ_KC * 2)), idesc, acc);
                         }
                     mma_commit(&empty[s]);
                 }
