@@ -128,6 +128,10 @@ struct fbt_ctx {
     // the line search just accepted) reuses it instead of regenerating and refactoring Sigma.
     bool factor_valid = false;
     double factor_theta[3] = {0.0, 0.0, 0.0};
+    // SA and SN hold Sigma_alpha, Sigma_nu at partials_theta (written together with Sigma by a
+    // line-search evaluation, so that Algorithm 3 at the accepted point generates nothing)
+    bool partials_valid = false;
+    double partials_theta[3] = {0.0, 0.0, 0.0};
     long long factor_reuses = 0;
 };
 
@@ -329,18 +333,27 @@ static bool theta_ok(const double* th) {
            th[2] > 0;
 }
 
-// Shared pipeline of Algorithms 2 and 3.
-static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
+static bool same_theta(const double a[3], const double b[3]) {
+    return a[0] == b[0] && a[1] == b[1] && a[2] == b[2];
+}
+
+// Shared pipeline of Algorithms 2 and 3.  keep_partials (Algorithm 2 only): generate Sigma_alpha
+// and Sigma_nu together with Sigma (the same exponentials serve all three) and keep them for an
+// Algorithm 3 evaluation at the same theta.
+static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv, bool keep_partials = false) {
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     Launcher L = launcher(c);
     const Geom& g = c->g;
     int rc = 0;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
-    const bool reuse = deriv && c->factor_valid && theta[0] == c->factor_theta[0] &&
-                       theta[1] == c->factor_theta[1] && theta[2] == c->factor_theta[2];
+    const bool reuse = deriv && c->factor_valid && same_theta(theta, c->factor_theta);
+    const bool have_partials = reuse && c->partials_valid && same_theta(theta, c->partials_theta);
+    const bool gen_partials = deriv ? !have_partials : (keep_partials && c->opts.with_derivatives);
     c->factor_valid = false;
+    if (deriv || gen_partials) c->partials_valid = false;     // SA, SN are about to change
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
-    if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, reuse ? nullptr : c->S, c->SA, c->SN, deriv,
+    if (!have_partials &&
+        (rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, reuse ? nullptr : c->S, c->SA, c->SN, gen_partials,
                               c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
     MixedPolicy pol;
@@ -383,6 +396,10 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv) {
     if (c->host_out.status & ST_BESSEL) return FBT_ERR_BESSEL;
     c->factor_valid = true;
     for (int i = 0; i < 3; ++i) c->factor_theta[i] = theta[i];
+    if (!deriv && gen_partials) {
+        c->partials_valid = true;
+        for (int i = 0; i < 3; ++i) c->partials_theta[i] = theta[i];
+    }
     return FBT_OK;
 }
 
@@ -393,9 +410,9 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
     const Geom& g = c->g;
     int rc = 0;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
-    const bool reuse = c->factor_valid && theta[0] == c->factor_theta[0] &&
-                       theta[1] == c->factor_theta[1] && theta[2] == c->factor_theta[2];
+    const bool reuse = c->factor_valid && same_theta(theta, c->factor_theta);
     c->factor_valid = false;
+    c->partials_valid = false;            // SA, SN receive L^-1 and Sigma^-1
     MixedPolicy pol;
     if (c->opts.precision == FBT_PREC_MIXED) {
         const double l2 = log2(c->opts.mixed_tol * theta[0]);
@@ -484,6 +501,7 @@ fbt_status fbt_generate(fbt_ctx* c, const double theta[3], int with_derivatives)
     Launcher L = launcher(c);
     int rc;
     c->factor_valid = false;
+    c->partials_valid = false;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
     if ((rc = launch_generate(L, c->g, c->X, c->Y, c->tc, c->qt, c->S, c->SA, c->SN,
@@ -599,6 +617,13 @@ const char* fbt_last_cuda_error(void) { return tl_cuda_error.c_str(); }
 }  // extern "C"
 
 namespace fbt {
+fbt_status loglik_keep_partials(fbt_ctx* c, const double theta[3], double* loglik) {
+    if (!c || !theta || !loglik) return FBT_ERR_ARG;
+    if (!theta_ok(theta)) { *loglik = -INFINITY; return FBT_ERR_DOMAIN; }
+    fbt_status st = evaluate(c, theta, false, true);
+    *loglik = st == FBT_OK ? c->host_out.loglik : -INFINITY;
+    return st;
+}
 cudaStream_t ctx_swap_stream(fbt_ctx* c, cudaStream_t s) {
     cudaStream_t prev = c->stream;
     c->stream = s;

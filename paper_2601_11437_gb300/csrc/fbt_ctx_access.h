@@ -8,4 +8,7 @@ namespace fbt {
 cudaStream_t ctx_swap_stream(fbt_ctx* c, cudaStream_t s);   // returns the previous stream
 int ctx_device(const fbt_ctx* c);
 long long ctx_n(const fbt_ctx* c);
+// Algorithm 2 that also generates Sigma_alpha, Sigma_nu at theta and keeps them for a following
+// Algorithm 3 evaluation at the same theta (the line search of Algorithm 1)
+fbt_status loglik_keep_partials(fbt_ctx* c, const double theta[3], double* loglik);
 }  // namespace fbt

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/fbt.h"
+#include "fbt_ctx_access.h"
 
 namespace {
 
@@ -227,7 +228,8 @@ fbt_status fisher_bt_step(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts* bto) {
     for (int it = 0; it <= bt.max_halvings; ++it) {
         for (int d = 0; d < 3; ++d) cand[d] = st->theta[d] + st->phi[d];
         double ll;
-        fbt_status s = mle_loglik(ctx, cand, &ll);
+        // the accepted candidate is evaluated next by Algorithm 3: keep its partials
+        fbt_status s = fbt::loglik_keep_partials(ctx, cand, &ll);
         st->n_ll += 1;
         if (hard_error(s)) return s;
         if (armijo_ok(s == FBT_OK ? ll : -INFINITY, st, st->phi, bt)) { accepted = true; break; }

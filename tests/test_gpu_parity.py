@@ -238,3 +238,28 @@ def test_mixed_path_matches_oracle_at_default_tolerance_and_emulated_when_strict
     loose = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_MIXED, mixed_tol=1e-6)
     c = fbt.mle_eval(loose, theta)
     assert c[0] != b[0] and abs(c[0] - b[0]) < 1e-3 * abs(b[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
+def test_line_search_partials_are_kept_for_the_accepted_point(precision):
+    # the line search's Algorithm 2 evaluation writes Sigma_alpha and Sigma_nu with Sigma; the
+    # Algorithm 3 evaluation at the accepted candidate then generates nothing, bitwise the same
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(500, 17, (1.0, 0.1, 0.9))
+    a = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    st = fbt.fisher_bt_start(a, (0.8, 0.08, 1.0))
+    fbt.fbt_profile(a, True)
+    fbt.fisher_bt_step(a, st)
+    prof = fbt.fbt_profile_read(a)
+    fbt.fbt_profile(a, False)
+    assert prof["generate_deriv"]["launches"] == st.halvings + 1
+    assert "generate" not in prof
+    b = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    ll, g, I = fbt.mle_eval(b, tuple(st.theta))
+    assert st.loglik == ll
+    assert np.array_equal(np.array(st.score[:]), g) and np.array_equal(np.array(st.fisher[:]).reshape(3, 3), I)
+    # a plain mle_loglik in between (another theta) leaves the kept partials usable only at theirs
+    th = tuple(st.theta)
+    fbt.mle_loglik(a, (0.7, 0.07, 0.9))
+    e = fbt.mle_eval(a, th)
+    assert e[0] == ll and np.array_equal(e[1], g)
