@@ -332,27 +332,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                         for (int j = 0; j < 8; ++j) v[g][j] = 0u;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    // exact group sums -> fixed point with unit 2^-46.  |acc_g| < 2^22 for g <= 1
-                    // (at most 2 products of < 2^21), so adding 1.5 * 2^23 in FP32 leaves the
-                    // integer in the low mantissa bits exactly; g = 2..4 (|acc| < 2^24) convert
-                    // with F2I; g = 5..7 enter fx only after a right shift by at least 3 bits, so
-                    // the ulp-4 rounding of adding 1.5 * 2^25 moves fx by at most 1/4 unit.
-                    long long hi = 0, lo = 0;
+                    // exact group sums -> fixed point with unit 2^-46.  Digits are below 2^7 in
+                    // magnitude, so group g (g + 1 products over K = 128) is below (g + 1) 2^21.
+                    // Group g carries weight 2^(32 - 7 g) units.  Groups 0, 1 (< 2^22) convert
+                    // exactly by adding 1.5 2^23 in FP32, groups 2..4 with F2I; groups 5..7 only
+                    // enter below the unit, so adding 1.5 2^25 (ulp 4, round to nearest even)
+                    // moves the result by at most 1/4 unit.  The pairs P = v_g 2^7 + v_(g+1)
+                    // are exact in 32-bit integers (|P67| < 7 2^28 + 2^24 + 2^8 < 2^31), and the
+                    // bits below one unit are rounded to nearest: the conversion has no bias.
+                    int iv[OZ_G];
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        const int iv = __float_as_int(__uint_as_float(v[g][j]) + 12582912.0f) - 0x4B400000;
-                        hi += (long long)iv * (1ll << (32 - 7 * g));
-                    }
+                    for (int g = 0; g < 2; ++g)
+                        iv[g] = __float_as_int(__uint_as_float(v[g][j]) + 12582912.0f) - 0x4B400000;
 #pragma unroll
-                    for (int g = 2; g < 4; ++g)
-                        hi += (long long)__float2int_rn(__uint_as_float(v[g][j])) * (1ll << (32 - 7 * g));
-                    lo += (long long)__float2int_rn(__uint_as_float(v[4][j])) * (1ll << 21);
+                    for (int g = 2; g < 5; ++g) iv[g] = __float2int_rn(__uint_as_float(v[g][j]));
 #pragma unroll
-                    for (int g = 5; g < OZ_G; ++g) {
-                        const int iv = (__float_as_int(__uint_as_float(v[g][j]) + 50331648.0f) - 0x4C400000) * 4;
-                        lo += (long long)iv * (1ll << (49 - 7 * g));
-                    }
-                    fx[cb + j] = hi + (lo >> 17);
+                    for (int g = 5; g < OZ_G; ++g)
+                        iv[g] = (__float_as_int(__uint_as_float(v[g][j]) + 50331648.0f) - 0x4C400000) * 4;
+                    const int p01 = iv[0] * 128 + iv[1], p23 = iv[2] * 128 + iv[3];
+                    const int p45 = iv[4] * 128 + iv[5], p67 = iv[6] * 128 + iv[7];
+                    const long long low = (long long)p45 * (1ll << 14) + p67 + (1ll << 16);
+                    fx[cb + j] = (long long)p01 * (1ll << 25) + (long long)p23 * (1ll << 11) + (low >> 17);
                 }
             }
             // accumulators are in registers: hand TMEM back to the MMA warp
