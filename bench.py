@@ -40,8 +40,8 @@ from paper_2601_11437_gb300 import inputs  # noqa: E402
 FIELDS = os.path.join(ROOT, "tests", "golden", "fields")
 METRIC = "Fisher-BT iterations/s (FP64 path)"
 PRECISIONS = {"fp64": 0, "fp64_emulated": 1}
-# tensor-core work of one emulated FP64 tile product: 36 BF16 digit products of the same shape
-OZAKI_PRODUCTS = 36
+# tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
+OZAKI_PRODUCTS = 28
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -252,7 +252,7 @@ def run_native(args):
                 "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
                                 else "fallback 1.7 PFLOP/s sustained") + " (of measured)",
-                "work": "36 BF16 digit products per FP64-accurate tile product",
+                "work": "28 BF16 digit products per FP64-accurate tile product",
                 "fp64_equivalent_tflops": fp64eq}
     else:
         roof = {"bound": "alu", "kernel": f"k_gemm_tile ({dom})", "achieved": fp64eq, "peak": FP64_PEAK_TFLOPS,
@@ -311,7 +311,7 @@ def run_native(args):
         "config": {"workload": w.name, "n": w.n, "nb": args.nb, "theta_true": w.theta_true,
                    "arithmetic": {"fp64": "FP64 DFMA tile updates",
                                   "fp64_emulated": "FP64-accurate tile updates from exact BF16 digit products "
-                                                   "on tcgen05 tensor cores (8 x 7-bit slices, FP32 TMEM groups, "
+                                                   "on tcgen05 tensor cores (7 x 8-bit balanced slices, FP32 TMEM groups, "
                                                    "FP64 recombination); all else FP64"}[args.precision],
                    "theta0": w.theta0, "jitter": w.jitter, "parallelism": f"replicas{world}",
                    "evaluations_per_step": evals / args.steps,

@@ -59,7 +59,7 @@ typedef struct {
     int device;           /* CUDA device ordinal; default 0                                        */
     int precision;        /* arithmetic of the tile updates: FBT_PREC_FP64 (default, FP64 DFMA),  */
                           /* FBT_PREC_FP64_EMULATED (FP64-accurate products on the BF16 tensor     */
-                          /* cores by 7-bit slicing) or FBT_PREC_MIXED (per tile product 8, 3 or 1 */
+                          /* cores by 8-bit slicing) or FBT_PREC_MIXED (per tile product 7, 3 or 1 */
                           /* digit planes, FP64 / FP32 / BF16-class, chosen from the operand tiles' */
                           /* largest entries against mixed_tol); the last two need nb = 128.       */
                           /* Diagonal-tile Cholesky, inverses, generation, solves of the field,   */

@@ -359,7 +359,9 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv, bool k
     MixedPolicy pol;
     if (c->opts.precision == FBT_PREC_MIXED) {
         // a tile product whose largest possible entry is below tol * sigma^2 * 2^6 may use one
-        // 7-bit digit plane, below tol * sigma^2 * 2^20 three planes (see MixedPolicy)
+        // 8-bit digit plane, below tol * sigma^2 * 2^20 three planes (see MixedPolicy); the
+        // thresholds were set for 7-bit digits and keep a factor 2 (one plane) to 2^3 (three)
+        // of margin with 8-bit ones
         const double l2 = log2(c->opts.mixed_tol * theta[0]);
         pol.on = 1;
         pol.e_fp32 = (int)floor(l2) - 1;

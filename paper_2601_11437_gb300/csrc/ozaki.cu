@@ -3,19 +3,21 @@
 // A tile update C -= op(A) op(B) with K = nb = 128 is computed as follows (the splitting scheme
 // of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012, carried out on tensor cores):
 //  1. Slicing.  Every row r of an operand (the dimension that survives into C) is scaled by
-//     s_r = 2^E_r with |x| < s_r for all its entries, and the scaled values u in (-1, 1) are cut
-//     into S = 8 signed 7-bit digits: u = sum_p d_p 2^(-7(p+1)) + O(2^-56), |d_p| <= 127.
-//     Digits are exact in BF16, and the cut is exact in FP64 (scaling by 2^k, truncation).
+//     s_r = 2^E_r with |x| < s_r for all its entries; the scaled magnitude, as the integer
+//     F = floor(|x| 2^(55 - E_r)) < 2^55, is written in S = 7 balanced 8-bit digits,
+//     F = sum_p d_p 2^(48 - 8p) with |d_p| <= 128, and the sign of x is applied to every digit:
+//     x = s_r sum_p d_p 2^(-8(p+1) + 1) up to the truncation below 2^-55 s_r.  Digits are exact
+//     in BF16 (at most 8 significant bits); the cut is exact integer arithmetic on the FP64 bits.
 //  2. Products.  For digit planes A_p, B_q the product A_p B_q^T over K = 128 is a sum of
-//     integers bounded by 128 * 127^2 < 2^21, so FP32 accumulation in TMEM is exact; all products
-//     of one "weight" g = p + q (at most 8 of them) share one accumulator and stay exact
-//     (8 * 2^21 <= 2^24).  The 36 products with g <= 7 are kept; the dropped ones are below
-//     2^-56 relative per element product, i.e. below FP64 rounding of the K-term dot product.
-//  3. Recombination.  The 8 exact group sums are combined in 64-bit integers (two words), then
-//     converted to FP64, scaled by s_r s_c 2^(-7(g+2)) and subtracted from the FP64 C.
-// The MMA is tcgen05.mma kind::f16 (BF16 in, FP32 out) M = 128, N = 32, K = 16, operands in
-// shared memory (canonical K-major core-matrix layout, no swizzle) filled by bulk copies
-// (cp.async.bulk, 1-D) from a pre-sliced panel buffer; accumulators live in tensor memory.
+//     integers bounded by 128 * 128^2 = 2^21, so FP32 accumulation in TMEM is exact; all products
+//     of one "weight" g = p + q (at most 7 of them) share one accumulator and stay exact
+//     (7 * 2^21 < 2^24).  The 28 products with g <= 6 are kept; the dropped ones are below
+//     2^-55 relative per element product, i.e. at FP64 rounding of the K-term dot product.
+//  3. Recombination.  The 7 exact group sums are combined in 64-bit fixed point, converted to
+//     FP64 (one rounding), scaled by s_r s_c and subtracted from the FP64 C.
+// The MMA is tcgen05.mma kind::f16 (BF16 in, FP32 out), M = 128, N = 64 .. 256, K = 16,
+// operands in shared memory (canonical K-major core-matrix layout, no swizzle) filled by bulk
+// copies (cp.async.bulk, 1-D) from a pre-sliced panel buffer; accumulators live in tensor memory.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -24,18 +26,19 @@
 
 namespace fbt {
 
-constexpr int OZ_S = 8;                      // digit planes per operand
-constexpr int OZ_G = 8;                      // accumulated weights g = 0..7
-constexpr int OZ_N = 64;                     // output columns per task (TMEM: 8 groups x 64 = 512 cols)
+constexpr int OZ_S = 7;                      // digit planes per operand
+constexpr int OZ_G = 7;                      // accumulated weights g = 0..6
+constexpr int OZ_N = 64;                     // output columns per task (TMEM: 7 groups x 64 columns)
+constexpr int OZ_TMEM_COLS = 512;            // allocation (a power of two >= 7 x 64)
 constexpr int OZ_KC = 16;                    // K per pipeline stage (one MMA K-step)
 constexpr int OZ_NKC = 128 / OZ_KC;          // stages per K = 128
 constexpr int OZ_CHUNK = 128 * OZ_KC * 2;    // bytes of one plane chunk: 128 rows x 16 K bf16
 constexpr int OZ_PLANE = OZ_NKC * OZ_CHUNK;  // 32 KB: one plane of a 128 x 128 tile
-constexpr size_t OZ_TILE_BYTES = (size_t)OZ_S * OZ_PLANE;   // 256 KB of digits per tile
-constexpr int OZ_STAGE_A = OZ_S * OZ_CHUNK;                  // 32 KB
-constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 16 KB
+constexpr size_t OZ_TILE_BYTES = (size_t)OZ_S * OZ_PLANE;   // 224 KB of digits per tile
+constexpr int OZ_STAGE_A = OZ_S * OZ_CHUNK;                  // 28 KB
+constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 14 KB
 constexpr int OZ_STAGES = 4;
-constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;   // 193 KB
+constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;   // 169 KB
 constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits
 
 size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }   // digits + row exponents
@@ -57,9 +60,9 @@ template <bool ROWS>
 __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ S, int T, int nb,
                                                      SliceJob job, unsigned char* __restrict__ dst) {
     // 4 CTAs per tile, 32 operand rows each; the digits are taken from the FP64 bit fields:
-    // |x| / 2^E_r = F 2^-56 with F = floor of the scaled magnitude (exact), digit p = bits
-    // 55-7p .. 49-7p of F with the sign of x -- the same digits as repeated truncation of
-    // u * 128 in FP64, without FP64 arithmetic.
+    // F = floor(|x| 2^(55 - E_r)) < 2^55 (exact), cut into 8-bit chunks from the least
+    // significant up; a chunk of 128 or more becomes chunk - 256 with a carry into the next, so
+    // every digit lies in [-128, 127] (the top one in [0, 128], as F < 2^55); then the sign of x.
     __shared__ int s_exp[32];
     const int t = blockIdx.x >> 2, rq = (blockIdx.x & 3) * 32;
     const double* X = job.tile_ptr(t, nb);
@@ -94,15 +97,18 @@ __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ 
             const unsigned long long b = (unsigned long long)__double_as_longlong(v);
             const int E = (int)((b >> 52) & 0x7FF);
             const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-            const int sh = 1019 + e - E;            // F = M * 2^(E - 1075 - e + 56)
+            const int sh = 1020 + e - E;            // F = M * 2^(E - 1075 - e + 55)
             unsigned long long F = 0;
             if (E != 0) F = sh < 0 ? (M << (-sh)) : (sh < 64 ? (M >> sh) : 0ull);
             const bool neg = (b >> 63) != 0;
+            int carry = 0;
 #pragma unroll
-            for (int p = 0; p < OZ_S; ++p) {
-                int d = (int)((F >> (49 - 7 * p)) & 127ull);
+            for (int p = OZ_S - 1; p >= 0; --p) {
+                int d = (int)((F >> (48 - 8 * p)) & 255ull) + carry;
+                carry = (p > 0 && d >= 128) ? 1 : 0;
+                d -= carry * 256;
                 d = neg ? -d : d;
-                const uint32_t h = __float_as_uint((float)d) >> 16;    // exact: |d| <= 127
+                const uint32_t h = __float_as_uint((float)d) >> 16;    // exact: |d| <= 128
                 if (j & 1) packed[p][j >> 1] |= h << 16;
                 else packed[p][j >> 1] = h;
             }
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(OZ_G * OZ_N));
+                     ::"r"(smem_u32(tmem_slot)), "r"(OZ_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -265,11 +271,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
         }
     } else if (warp == 0) {
         if (lane == 0) {
-            // MMA issuer: per stage the 36 digit products with p + q <= 7 into group g = p + q.
+            // MMA issuer: per stage the 28 digit products with p + q <= 6 into group g = p + q.
             // The groups occupy consecutive 64-column ranges of TMEM and the B planes consecutive
             // 64-row blocks of the stage, so the products (p, q0 .. q1) are one MMA with
-            // N = 64 (q1 - q0 + 1) <= 256 into the columns of groups p + q0 .. p + q1: 12 MMAs
-            // per stage instead of 36, and A_p is read from shared memory once per MMA.
+            // N = 64 (q1 - q0 + 1) <= 256 into the columns of groups p + q0 .. p + q1: 10 MMAs
+            // per stage instead of 28, and A_p is read from shared memory once per MMA.
             const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
             long long it = 0, nt = 0;
             for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
@@ -332,27 +338,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                         for (int j = 0; j < 8; ++j) v[g][j] = 0u;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    // exact group sums -> fixed point with unit 2^-46.  Digits are below 2^7 in
-                    // magnitude, so group g (g + 1 products over K = 128) is below (g + 1) 2^21.
-                    // Group g carries weight 2^(32 - 7 g) units.  Groups 0, 1 (< 2^22) convert
-                    // exactly by adding 1.5 2^23 in FP32, groups 2..4 with F2I; groups 5..7 only
-                    // enter below the unit, so adding 1.5 2^25 (ulp 4, round to nearest even)
-                    // moves the result by at most 1/4 unit.  The pairs P = v_g 2^7 + v_(g+1)
-                    // are exact in 32-bit integers (|P67| < 7 2^28 + 2^24 + 2^8 < 2^31), and the
-                    // bits below one unit are rounded to nearest: the conversion has no bias.
-                    int iv[OZ_G];
-#pragma unroll
-                    for (int g = 0; g < 2; ++g)
-                        iv[g] = __float_as_int(__uint_as_float(v[g][j]) + 12582912.0f) - 0x4B400000;
-#pragma unroll
-                    for (int g = 2; g < 5; ++g) iv[g] = __float2int_rn(__uint_as_float(v[g][j]));
-#pragma unroll
-                    for (int g = 5; g < OZ_G; ++g)
-                        iv[g] = (__float_as_int(__uint_as_float(v[g][j]) + 50331648.0f) - 0x4C400000) * 4;
-                    const int p01 = iv[0] * 128 + iv[1], p23 = iv[2] * 128 + iv[3];
-                    const int p45 = iv[4] * 128 + iv[5], p67 = iv[6] * 128 + iv[7];
-                    const long long low = (long long)p45 * (1ll << 14) + p67 + (1ll << 16);
-                    fx[cb + j] = (long long)p01 * (1ll << 25) + (long long)p23 * (1ll << 11) + (low >> 17);
+                    // exact group sums -> fixed point with unit 2^-46 of s_r s_c.  Group g (at
+                    // most g + 1 products of digits <= 2^7 over K = 128) is below (g + 1) 2^21 and
+                    // carries weight 2^(32 - 8 g) units.  Group 0 (<= 2^21) converts exactly by
+                    // adding 1.5 2^23 in FP32, groups 1..4 with F2I; groups 5, 6 only enter below
+                    // the unit, so adding 1.5 2^25 (ulp 4, round to nearest even) moves the result
+                    // by at most 2^-7 unit.  P = v_g 2^8 + v_(g+1) for g = 0, 2 is exact in 32-bit
+                    // integers (|P23| <= 3 2^29 + 2^23 < 2^31), and the bits below one unit are
+                    // rounded to nearest: the conversion has no bias.
+                    const int iv0 = __float_as_int(__uint_as_float(v[0][j]) + 12582912.0f) - 0x4B400000;
+                    const int iv1 = __float2int_rn(__uint_as_float(v[1][j]));
+                    const int iv2 = __float2int_rn(__uint_as_float(v[2][j]));
+                    const int iv3 = __float2int_rn(__uint_as_float(v[3][j]));
+                    const int iv4 = __float2int_rn(__uint_as_float(v[4][j]));
+                    const int iv5 = (__float_as_int(__uint_as_float(v[5][j]) + 50331648.0f) - 0x4C400000) * 4;
+                    const int iv6 = (__float_as_int(__uint_as_float(v[6][j]) + 50331648.0f) - 0x4C400000) * 4;
+                    const int p01 = iv0 * 256 + iv1, p23 = iv2 * 256 + iv3;
+                    const long long low = (long long)iv5 * 256 + iv6 + (1ll << 15);
+                    fx[cb + j] = (long long)p01 * (1ll << 24) + (long long)p23 * (1ll << 8) + iv4 + (low >> 16);
                 }
             }
             // accumulators are in registers: hand TMEM back to the MMA warp
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
     if (*fail && tid == 0) atomicOr(status, ST_TIMEOUT);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_G * OZ_N));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
     }
 }
 
