@@ -22,17 +22,16 @@ enum : int { ST_NOT_PD = 1, ST_BESSEL = 2, ST_DOMAIN = 4, ST_TIMEOUT = 8 };
 // ---- arithmetic of the tile updates ----
 enum : int { PREC_FP64 = 0, PREC_FP64_OZAKI = 1, PREC_MIXED = 2 };
 
-// Mixed path: a tile product with operand maxima 2^ea, 2^eb uses 8 digit planes (FP64-accurate)
-// if ea + eb >= e_fp64, 3 planes (21 bits, FP32-class) if ea + eb >= e_fp32, else 1 plane
-// (7 bits, BF16-class).  Thresholds come from the context's tau_fp64 / tau_fp32 relative to
-// sigma^2: e = ceil(log2(tau * sigma^2)) - 7 (the 7 accounts for the K = 128 terms).
+// Mixed path: a tile product with operand maxima 2^ea, 2^eb uses all 7 digit planes
+// (FP64-accurate) if ea + eb >= e_fp64, 3 planes (24 bits, FP32-class) if ea + eb >= e_fp32,
+// else 1 plane (8 bits, BF16-class); the thresholds follow from mixed_tol * sigma^2.
 struct MixedPolicy {
     int on = 0;
     int e_fp64 = 0, e_fp32 = 0;
 };
 
 // ---- trapezoid quadrature of K_nu, K_{nu-1} and dK_nu/dnu (see matern_gen.cu) ----
-constexpr int QUAD_LEVELS = 4;
+constexpr int QUAD_LEVELS = 5;
 constexpr int QUAD_NODES = 256;
 
 struct ThetaConsts {
@@ -43,9 +42,9 @@ struct ThetaConsts {
     double jitter;
 };
 
-constexpr int EXP_TABLE = 64;
+constexpr int EXP_TABLE = 256;
 struct QuadTables {
-    double exp2tab[EXP_TABLE];            // 2^(j/64), j = 0..63 (table of the exponential)
+    double exp2tab[EXP_TABLE];            // 2^(j/256), j = 0..255 (table of the exponential)
     double st2[QUAD_LEVELS][QUAD_NODES];  // 2 sinh^2(t_j / 2)  (x cosh t = x + x * st2)
     double wa[QUAD_LEVELS][QUAD_NODES];   // w_j cosh(nu t_j)
     double wb[QUAD_LEVELS][QUAD_NODES];   // w_j cosh((nu - 1) t_j)

@@ -9,8 +9,13 @@
 
 namespace fbt {
 
-static __constant__ double c_level_h[QUAD_LEVELS] = {0.15, 0.075, 0.0375, 0.01875};
-static __constant__ double c_level_xmax[QUAD_LEVELS] = {20.0, 80.0, 320.0, 1280.0};
+// Step h of each level and the largest x it serves.  For large x the discretisation error is
+// about exp(-2 pi^2 / (h^2 x)) (the integrand is close to a Gaussian of variance 1 / x), below
+// 1e-18 while h^2 x <= 0.476; for small x it is about exp(-2 pi d / h) with d just below pi / 2,
+// the half-width of the strip where the integrand stays analytic and decaying: below 1e-18 for
+// h <= 0.2 (the level h = 0.2 serves x <= 11).
+static __constant__ double c_level_h[QUAD_LEVELS] = {0.2, 0.15, 0.075, 0.0375, 0.01875};
+static __constant__ double c_level_xmax[QUAD_LEVELS] = {11.0, 20.0, 80.0, 320.0, 1280.0};
 constexpr double X_ZERO_BELOW = 2.5e-15;   // x smaller than this: coincident points, R = 1
 constexpr double X_UNDERFLOW = 720.0;      // x larger than this: R and partials underflow to 0
 constexpr double STOP_REL = 1e-17;
@@ -29,18 +34,18 @@ static __device__ double digamma_pos(double x) {
 
 // e^a for a <= 0 by table-driven argument reduction (P. T. P. Tang, "Table-driven implementation
 // of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
-// a = (64 m + j) ln2/64 + r with |r| <= ln2/128, e^a = 2^m 2^(j/64) e^r, e^r - 1 by its degree-5
-// Taylor polynomial (truncation < 4e-17 relative), ln2/64 split into a 36-bit head (n * head is
-// exact for |n| < 2^17) and a tail, 2^m applied to the exponent field.  Error ~2 ulp.
+// a = (256 m + j) ln2/256 + r with |r| <= ln2/512, e^a = 2^m 2^(j/256) e^r, e^r - 1 by its
+// degree-4 Taylor polynomial (truncation below 4e-17 relative, odd in r), ln2/256 split into a
+// 35-bit head (n * head is exact for |n| < 2^18) and a tail, 2^m applied to the exponent field.
 __device__ __forceinline__ double exp_nonpos(double a, const double* __restrict__ tab) {
     if (a < -700.0) return 0.0;                                 // keeps 2^m y a normal number
-    const double n = rint(a * 92.33248261689366);               // 64 / ln 2
-    double r = fma(-n, 0x1.62e42fefa0000p-7, a);               // ln 2 / 64, head
-    r = fma(-n, 0x1.cf79abc9e3b3ap-46, r);                      // ln 2 / 64, tail
+    const double n = rint(a * 369.3299304675746);              // 256 / ln 2
+    double r = fma(-n, 0x1.62e42fefc0000p-9, a);               // ln 2 / 256, head
+    r = fma(-n, -0x1.c610ca86c3899p-45, r);                     // ln 2 / 256, tail
     const int ni = (int)n;
-    const int j = ni & (EXP_TABLE - 1), m = ni >> 6;
-    const double p = r * fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0);
-    const double y = fma(tab[j], p, tab[j]);                    // 2^(j/64) e^r in [1, 2)
+    const int j = ni & (EXP_TABLE - 1), m = ni >> 8;
+    const double p = r * fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0);
+    const double y = fma(tab[j], p, tab[j]);                    // 2^(j/256) e^r in [1, 2)
     return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
 }
 
@@ -57,27 +62,25 @@ __device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& t
     MaternVals v{0.0, 0.0, 0.0};
     if (x < X_ZERO_BELOW) { v.r = 1.0; return v; }
     if (x > X_UNDERFLOW) return v;
-    int l = x <= c_level_xmax[0] ? 0 : x <= c_level_xmax[1] ? 1 : x <= c_level_xmax[2] ? 2 : 3;
+    int l = x <= c_level_xmax[0] ? 0 : x <= c_level_xmax[1] ? 1 : x <= c_level_xmax[2] ? 2 : x <= c_level_xmax[3] ? 3 : 4;
     const int base = l * QUAD_NODES;
     double sa = 0.0, sb = 0.0, sd = 0.0;
     // four nodes per round; the stopping test (last terms below STOP_REL of the sums, which
     // can only happen past the integrand's peak) is evaluated once per round
     for (int j = 0; j < QUAD_NODES; j += 4) {
-        double ta = 0.0, tb = 0.0, td = 0.0;
+        double e = 0.0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const double e = exp_nonpos(-x * st2[base + j + u], etab);
-            ta = e * wa[base + j + u];
-            sa += ta;
+            e = exp_nonpos(-x * st2[base + j + u], etab);
+            sa = fma(e, wa[base + j + u], sa);
             if (DERIV) {
-                tb = e * wb[base + j + u];
-                td = e * wd[base + j + u];
-                sb += tb;
-                sd += td;
+                sb = fma(e, wb[base + j + u], sb);
+                sd = fma(e, wd[base + j + u], sd);
             }
         }
-        bool done = ta <= STOP_REL * sa;
-        if (DERIV) done = done && tb <= STOP_REL * sb && td <= STOP_REL * sd;
+        // the round's last terms against the sums (the terms decrease past the peak)
+        bool done = e * wa[base + j + 3] <= STOP_REL * sa;
+        if (DERIV) done = done && e * wb[base + j + 3] <= STOP_REL * sb && e * wd[base + j + 3] <= STOP_REL * sd;
         if (done) break;
     }
     const double lx = log(x);

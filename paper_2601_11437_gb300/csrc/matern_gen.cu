@@ -13,8 +13,9 @@
 // branch-uniform rule; its truncated series agree with it to their truncation error).  The node
 // weights w_j f(t_j) depend only on theta and are tabulated once per evaluation; the step h of
 // a level bounds the discretisation error (about exp(-2 pi^2 / (h^2 x)) for large x and
-// exp(-2 pi d / h) for small x) below 1e-17 relative: h = 0.15 for x <= 20, halved each time
-// the range grows 4x.  Each sum stops once its term drops below 1e-17 of its running value.
+// exp(-2 pi d / h) for small x) below 1e-17 relative: h = 0.2 for x <= 11, 0.15 for x <= 20,
+// then halved each time the range grows 4x.  Each sum stops once its term drops below 1e-17 of
+// its running value.
 #include <math.h>
 
 #include "fbt_kernels.cuh"

@@ -44,9 +44,9 @@ __global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int 
         if (threadIdx.x == 0) {
             double d = A[j + j * LD];
             if (!(d > 0.0) || !isfinite(d)) { s_bad = 1; d = 1.0; }
-            const double l = sqrt(d);
-            A[j + j * LD] = l;
-            s_inv = 1.0 / l;
+            const double inv = rsqrt(d);             // one long-latency FP64 operation on the
+            A[j + j * LD] = d * inv;                 // sequential chain instead of sqrt and 1 / l
+            s_inv = inv;
         }
         __syncthreads();
         for (int r = j + 1 + threadIdx.x; r < NB; r += blockDim.x) A[r + j * LD] *= s_inv;
@@ -105,8 +105,9 @@ int strips_per_tile(int nb) { return nb / STRIP; }
 
 template <int NB, bool LEFT, int NMAT, int EPI>
 __global__ void __launch_bounds__(256) k_trsm_strip(TrsmParams p) {
-    extern __shared__ double V[];                      // [NMAT][STRIP][NB + 1]
+    extern __shared__ double V[];                      // [NMAT][STRIP][NB + 1], then L [NB][NB + 1]
     constexpr int LDV = NB + 1;
+    double* Ls = V + NMAT * STRIP * LDV;               // the triangular factor, staged once
     constexpr int NSTRIPS = NB / STRIP;
     __shared__ double s_inv[NB];
     __shared__ double s_red[STRIP][8];
@@ -136,12 +137,16 @@ __global__ void __launch_bounds__(256) k_trsm_strip(TrsmParams p) {
             V[(m * STRIP + lane) * LDV + d] = val;
         }
     }
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e % NB, c = e / NB;
+        if (r > c) Ls[r + c * LDV] = Lt[e];
+    }
     for (int d = threadIdx.x; d < NB; d += blockDim.x) s_inv[d] = 1.0 / Lt[d + (long long)d * NB];
     __syncthreads();
     const int lane = threadIdx.x % STRIP, grp = threadIdx.x / STRIP;   // 8 groups of 32
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int d = 0; d < NB; ++d) {
-        const double* __restrict__ Lcol = Lt + (long long)d * NB;
+        const double* __restrict__ Lcol = Ls + d * LDV;
         double vv[NMAT];
 #pragma unroll
         for (int m = 0; m < NMAT; ++m) vv[m] = V[(m * STRIP + lane) * LDV + d] * s_inv[d];
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(256) k_trsm_strip(TrsmParams p) {
             }
         }
         for (int dp = d + 1 + grp; dp < NB; dp += 8) {
-            const double l = __ldg(Lcol + dp);
+            const double l = Lcol[dp];
 #pragma unroll
             for (int m = 0; m < NMAT; ++m) V[(m * STRIP + lane) * LDV + dp] -= vv[m] * l;
         }
@@ -321,7 +326,7 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
                       int precision, unsigned char* slices, const MixedPolicy& pol) {
     const int T = g.T;
     const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
-    const size_t smem_trsm1 = (size_t)STRIP * (NB + 1) * sizeof(double);
+    const size_t smem_trsm1 = (size_t)(STRIP + NB) * (NB + 1) * sizeof(double);
     cudaFuncSetAttribute(k_potrf_diag<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_potrf);
     cudaFuncSetAttribute(k_trsm_strip<NB, false, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_trsm1);
     constexpr int NS = NB / STRIP;
@@ -619,7 +624,7 @@ static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, d
     const int T = g.T;
     constexpr int NS = NB / STRIP;
     constexpr int SB = NB / GB;
-    const size_t smem2 = (size_t)2 * STRIP * (NB + 1) * sizeof(double);
+    const size_t smem2 = (size_t)(2 * STRIP + NB) * (NB + 1) * sizeof(double);
     cudaFuncSetAttribute(k_trsm_strip<NB, false, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);

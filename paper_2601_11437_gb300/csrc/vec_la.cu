@@ -20,11 +20,13 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
     // inside the sequential loop
     extern __shared__ double A[];
     const int LD = nb + 1;
-    const double* __restrict__ Lt = S + tile_offset(m, m, T, nb);
+    double* rinv = A + nb * LD;                // 1 / L_dd, computed in parallel before the
+    const double* __restrict__ Lt = S + tile_offset(m, m, T, nb);   // sequential loop
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         const int r = e % nb, c = e / nb;
         if (r >= c) A[r + c * LD] = Lt[e];
     }
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) rinv[d] = 1.0 / Lt[d + (long long)d * nb];
     __syncthreads();
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
             for (int dd = 0; dd < 32; ++dd) {
                 const int d = 32 * s + dd;
                 double xd = 0.0;
-                if (lane == dd) { xd = x[s] / A[d + d * LD]; x[s] = xd; }
+                if (lane == dd) { xd = x[s] * rinv[d]; x[s] = xd; }
                 xd = __shfl_sync(0xffffffffu, xd, dd);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
             for (int dd = 31; dd >= 0; --dd) {
                 const int d = 32 * s + dd;
                 double xd = 0.0;
-                if (lane == dd) { xd = x[s] / A[d + d * LD]; x[s] = xd; }
+                if (lane == dd) { xd = x[s] * rinv[d]; x[s] = xd; }
                 xd = __shfl_sync(0xffffffffu, xd, dd);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -71,30 +73,42 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
         if (s < nblk) vm[lane + 32 * s] = x[s];
 }
 
-// forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i, thread per row)
-// backward: v_p -= L(m, p)^T v_m for p < m (one CTA per tile p, warp per column)
+// forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i)
+// backward: v_p -= L(m, p)^T v_m for p < m (one CTA per tile p)
+// Each of the 8 warps takes nb / 8 columns of the tile, so every thread has nb / 8 independent
+// loads in flight; the warps' partial sums are added in a fixed order.
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ S, int T, int nb,
                                                      int m, double* __restrict__ v) {
-    extern __shared__ double sv[];
+    extern __shared__ double sv[];            // v_m [nb], then partial sums [8][nb]
+    double* part = sv + nb;
     const double* vm = v + (long long)m * nb;
     for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw = nb / 8, cbeg = warp * cw;
     if (!TRANS) {
         const int i = m + 1 + blockIdx.x;
         const double* __restrict__ A = S + tile_offset(i, m, T, nb);
+        for (int r = lane; r < nb; r += 32) {          // rows r of columns cbeg .. cbeg + cw - 1
+            double acc = 0.0;
+#pragma unroll 8
+            for (int c = cbeg; c < cbeg + cw; ++c) acc = fma(A[r + (long long)c * nb], sv[c], acc);
+            part[warp * nb + r] = acc;
+        }
+        __syncthreads();
         double* vi = v + (long long)i * nb;
         for (int r = threadIdx.x; r < nb; r += blockDim.x) {
             double acc = 0.0;
-            for (int c = 0; c < nb; ++c) acc = fma(A[r + (long long)c * nb], sv[c], acc);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) acc += part[w * nb + r];
             vi[r] -= acc;
         }
     } else {
         const int pt = blockIdx.x;
         const double* __restrict__ A = S + tile_offset(m, pt, T, nb);
         double* vp = v + (long long)pt * nb;
-        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-        for (int c = warp; c < nb; c += nw) {
+        for (int c = cbeg; c < cbeg + cw; ++c) {       // column c of L(m, p): a dot with v_m
             double acc = 0.0;
             for (int r = lane; r < nb; r += 32) acc = fma(A[r + (long long)c * nb], sv[r], acc);
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -105,8 +119,8 @@ __global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ 
 
 int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans) {
     const int T = g.T, nb = g.nb;
-    const size_t smem = (size_t)nb * sizeof(double);
-    const size_t smem_diag = (size_t)nb * (nb + 1) * sizeof(double);
+    const size_t smem_upd = (size_t)nb * 9 * sizeof(double);
+    const size_t smem_diag = (size_t)nb * (nb + 2) * sizeof(double);
     cudaFuncSetAttribute(k_trsv_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     cudaFuncSetAttribute(k_trsv_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
     const double tb = 8.0 * nb * nb;
@@ -117,7 +131,7 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
             k_trsv_diag<false><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m + 1 < T) {
-                k_trsv_update<false><<<T - m - 1, 256, smem, L.stream>>>(S, T, nb, m, v);
+                k_trsv_update<false><<<T - m - 1, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
                 L.count();
             }
         }
@@ -126,7 +140,7 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
             k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m > 0) {
-                k_trsv_update<true><<<m, 256, smem, L.stream>>>(S, T, nb, m, v);
+                k_trsv_update<true><<<m, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
                 L.count();
             }
         }
