@@ -34,9 +34,15 @@ __global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int 
     __shared__ double s_inv;
     __shared__ int s_bad;
     double* tile = S + tile_offset(k, k, T, NB);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        A[r + c * LD] = r >= c ? tile[e] : 0.0;
+    {
+        const double2* __restrict__ t2 = (const double2*)tile;
+#pragma unroll 16
+        for (int e2 = threadIdx.x; e2 < NB * NB / 2; e2 += blockDim.x) {
+            const double2 w = t2[e2];
+            const int r = (2 * e2) % NB, c = (2 * e2) / NB;
+            A[r + c * LD] = r >= c ? w.x : 0.0;
+            A[r + 1 + c * LD] = r + 1 >= c ? w.y : 0.0;
+        }
     }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
@@ -60,9 +66,13 @@ __global__ void __launch_bounds__(512) k_potrf_diag(double* __restrict__ S, int 
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        tile[e] = r >= c ? A[r + c * LD] : 0.0;
+    {
+        double2* t2 = (double2*)tile;
+#pragma unroll 16
+        for (int e2 = threadIdx.x; e2 < NB * NB / 2; e2 += blockDim.x) {
+            const int r = (2 * e2) % NB, c = (2 * e2) / NB;
+            t2[e2] = make_double2(r >= c ? A[r + c * LD] : 0.0, r + 1 >= c ? A[r + 1 + c * LD] : 0.0);
+        }
     }
     // sum of log L_jj: one logarithm per thread, then a fixed-order tree
     __shared__ double s_log[NB];
@@ -137,9 +147,15 @@ __global__ void __launch_bounds__(256) k_trsm_strip(TrsmParams p) {
             V[(m * STRIP + lane) * LDV + d] = val;
         }
     }
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        if (r > c) Ls[r + c * LDV] = Lt[e];
+    {
+        const double2* __restrict__ L2 = (const double2*)Lt;
+#pragma unroll 16
+        for (int e2 = threadIdx.x; e2 < NB * NB / 2; e2 += blockDim.x) {
+            const double2 w = L2[e2];
+            const int r = (2 * e2) % NB, c = (2 * e2) / NB;
+            if (r > c) Ls[r + c * LDV] = w.x;
+            if (r + 1 > c) Ls[r + 1 + c * LDV] = w.y;
+        }
     }
     for (int d = threadIdx.x; d < NB; d += blockDim.x) s_inv[d] = 1.0 / Lt[d + (long long)d * NB];
     __syncthreads();

@@ -22,9 +22,14 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
     const int LD = nb + 1;
     double* rinv = A + nb * LD;                // 1 / L_dd, computed in parallel before the
     const double* __restrict__ Lt = S + tile_offset(m, m, T, nb);   // sequential loop
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int r = e % nb, c = e / nb;
-        if (r >= c) A[r + c * LD] = Lt[e];
+    // 16-byte loads, many in flight per thread: one CTA must pull the whole tile
+    const double2* __restrict__ L2 = (const double2*)Lt;
+#pragma unroll 16
+    for (int e2 = threadIdx.x; e2 < nb * nb / 2; e2 += blockDim.x) {
+        const double2 w = L2[e2];
+        const int r = (2 * e2) % nb, c = (2 * e2) / nb;
+        if (r >= c) A[r + c * LD] = w.x;
+        if (r + 1 >= c) A[r + 1 + c * LD] = w.y;
     }
     for (int d = threadIdx.x; d < nb; d += blockDim.x) rinv[d] = 1.0 / Lt[d + (long long)d * nb];
     __syncthreads();
