@@ -18,7 +18,8 @@ class NotPositiveDefinite(ArithmeticError):
 
 def cholesky(A: np.ndarray, nb: int = 64, overwrite: bool = False) -> np.ndarray:
     """Lower-triangular L with A = L L^T, right-looking blocked algorithm (overwrite: factor A's
-    own storage in place, for matrices too large to copy)."""
+    own storage in place, for matrices too large to copy, updating only the lower part of the
+    trailing matrix, a block of columns at a time)."""
     W = A if overwrite else np.array(A, dtype=np.float64, copy=True)
     n = W.shape[0]
     for k0 in range(0, n, nb):
@@ -32,7 +33,12 @@ def cholesky(A: np.ndarray, nb: int = 64, overwrite: bool = False) -> np.ndarray
         for j in range(k0, k1):                      # panel below: X L_kk^T = A_panel
             W[k1:, j] = (W[k1:, j] - W[k1:, k0:j] @ W[j, k0:j]) / W[j, j]
         P = W[k1:, k0:k1]
-        W[k1:, k1:] -= P @ P.T                       # trailing update
+        if overwrite:                                # trailing update, lower part, column chunks
+            for c0 in range(k1, n, 4 * nb):          # (no (n - k1)^2 temporary)
+                c1 = min(n, c0 + 4 * nb)
+                W[c0:, c0:c1] -= P[c0 - k1:] @ P[c0 - k1:c1 - k1].T
+        else:
+            W[k1:, k1:] -= P @ P.T                   # trailing update
     if overwrite:
         for k0 in range(0, n, nb):                   # zero the strict upper triangle in blocks
             k1 = min(n, k0 + nb)
