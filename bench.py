@@ -473,6 +473,57 @@ def run_adjoint(args):
     return 0
 
 
+def run_compare(args):
+    """Mixed against emulated FP64 on one large field: l, score, Fisher at theta^(0), the Cholesky
+    rate, and the Fisher-BT estimate of each path (Algorithm 1 to convergence)."""
+    import torch
+    import paper_2601_11437_gb300 as fbt
+    w, locs, z = load_field(args.workload)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp64_emulated", fbt.PREC_FP64_EMULATED), ("mixed", fbt.PREC_MIXED)):
+        ctx = fbt.fbt_create(locs, z, nb=128, precision=prec)
+        fbt.mle_loglik(ctx, np.array(w.theta0) * 1.01)             # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fbt.fbt_profile(ctx, True)
+        ev[0].record(stream)
+        fbt.mle_loglik(ctx, w.theta0)
+        ev[1].record(stream)
+        ll, g, I = fbt.mle_eval(ctx, w.theta0)                      # reuses the factor
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        prof = fbt.fbt_profile_read(ctx)
+        fbt.fbt_profile(ctx, False)
+        chol = {k: v for k, v in prof.items() if k in ("potrf_diag", "trsm_panel", "ozaki_potrf_update", "ozaki_slice")}
+        # the slicing of the Cholesky's panels is counted with the Cholesky (the transforms' slices are not)
+        chol_ms = sum(v["ms"] for k, v in chol.items() if k != "ozaki_slice")
+        n = w.n
+        t0 = time.perf_counter()
+        st = fbt.fisher_bt_run(ctx, theta0=w.theta0)
+        torch.cuda.synchronize()
+        fit_s = time.perf_counter() - t0
+        out[name] = {"loglik_s": ev[0].elapsed_time(ev[1]) / 1e3, "mle_eval_s": ev[1].elapsed_time(ev[2]) / 1e3,
+                     "cholesky_tflops_fp64_equivalent": (n ** 3 / 3) / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e12,
+                     "cholesky_kernel_ms": chol_ms,
+                     "loglik": ll, "score": g.tolist(), "fisher": I.tolist(),
+                     "theta_hat": list(st.theta), "state": st.state, "iterations": st.iter,
+                     "n_ll": st.n_ll, "n_grad": st.n_grad, "fit_s": fit_s,
+                     "fisher_bt_iters_per_s": st.iter / fit_s if st.iter else None}
+        fbt.fbt_destroy(ctx)
+    e, m = out["fp64_emulated"], out["mixed"]
+    rel = lambda a, b: float(np.max(np.abs(np.array(a) - np.array(b))) / np.max(np.abs(np.array(b))))  # noqa: E731
+    line = {"metric": "mixed vs FP64-accurate path", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "theta0": w.theta0, "theta_true": w.theta_true,
+                       "mixed_tol": 1e-12},
+            "rel_err_loglik": abs(m["loglik"] - e["loglik"]) / abs(e["loglik"]),
+            "rel_err_score": rel(m["score"], e["score"]), "rel_err_fisher": rel(m["fisher"], e["fisher"]),
+            "rel_err_theta_hat": rel(m["theta_hat"], e["theta_hat"]),
+            "speedup_mle_eval": e["mle_eval_s"] / m["mle_eval_s"], "speedup_loglik": e["loglik_s"] / m["loglik_s"],
+            "paths": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,11 +539,15 @@ def main():
     ap.add_argument("--reference-n", type=int, default=1536)
     ap.add_argument("--threads", type=int, default=16, help="host threads of the batched workload")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
+    ap.add_argument("--compare-mixed", action="store_true",
+                    help="mixed against emulated FP64 on --workload (errors, Cholesky rate, estimates)")
     args = ap.parse_args()
     if args.workload.startswith("batch") and args.impl == "native":
         return run_batch(args)
     if args.adjoint:
         return run_adjoint(args)
+    if args.compare_mixed:
+        return run_compare(args)
     if args.warmup < 3 and args.impl == "native" and not os.environ.get("FBT_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     return run_reference(args) if args.impl == "reference" else run_native(args)
