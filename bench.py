@@ -524,6 +524,55 @@ def run_compare(args):
     return 0
 
 
+def run_sim(args):
+    """The simulation study (Sec. 3): every stored realisation of every (setting, n) fitted by
+    Algorithm 1 from the L9 design over the study's box, realisations of one (setting, n) as one
+    batch; per (setting, n) the estimates' mean and spread, the microergodic theta_m =
+    sigma^2 alpha^(-2 nu), iterations, l and derivative calls, Nelder-Mead shifts and time."""
+    import torch
+    import paper_2601_11437_gb300 as fbt
+    meta = json.load(open(os.path.join(FIELDS, f"{args.workload}_z.json")))
+    zall = np.load(os.path.join(FIELDS, f"{args.workload}_z.npy"))
+    reps = meta["reps"]
+    prec = PRECISIONS[args.precision]
+    lo, hi = np.array(inputs.SIM_BOX[0]), np.array(inputs.SIM_BOX[1])
+    h, o, rows = hashlib.sha256(), 0, []
+    t_all = time.perf_counter()
+    for n in inputs.SIM_SIZES:
+        locs = inputs.sim_locations(n)
+        h.update(np.ascontiguousarray(locs, dtype="<f8").tobytes())
+        for si, th in enumerate(inputs.SIM_SETTINGS):
+            zs = [zall[o + r * n:o + (r + 1) * n] for r in range(reps)]
+            o += reps * n
+            ctxs = [fbt.fbt_create(locs, z, nb=args.nb, precision=prec) for z in zs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            states, status = fbt.fisher_bt_run_batch(ctxs, theta_lo=np.tile(lo, (reps, 1)),
+                                                     theta_hi=np.tile(hi, (reps, 1)), nthreads=args.threads)
+            dt = time.perf_counter() - t0
+            for c in ctxs:
+                fbt.fbt_destroy(c)
+            est = np.array([list(st.theta) for st in states])
+            tm = est[:, 0] * est[:, 1] ** (-2 * est[:, 2])
+            rows.append({
+                "n": n, "theta_true": th, "theta_m_true": th[0] * th[1] ** (-2 * th[2]),
+                "theta_hat_mean": est.mean(0).round(6).tolist(), "theta_hat_sd": est.std(0, ddof=1).round(6).tolist(),
+                "theta_m_mean": float(np.mean(tm)), "theta_m_sd": float(np.std(tm, ddof=1)),
+                "iterations_mean": float(np.mean([st.iter for st in states])),
+                "l_calls_mean": float(np.mean([st.n_ll for st in states])),
+                "derivative_calls_mean": float(np.mean([st.n_grad for st in states])),
+                "nelder_mead_fraction": float(np.mean([st.state == fbt.DONE_NM for st in states])),
+                "failed": int(np.sum([(st.state == fbt.FAILED) or s_ != fbt.FBT_OK for st, s_ in zip(states, status)])),
+                "seconds_per_fit_in_batch": dt / reps, "batch_seconds": dt})
+    if h.hexdigest() != meta["locations_sha256"] or o != zall.size:
+        raise RuntimeError(f"stored {args.workload} does not belong to these designs")
+    line = {"metric": "simulation study (Sec. 3): Fisher-BT fits from the L9 design", "n_gpus": 1,
+            "dtype": "f64", "data": "synthetic", "precision": args.precision, "reps": reps,
+            "box": inputs.SIM_BOX, "total_seconds": time.perf_counter() - t_all, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,6 +593,8 @@ def main():
     args = ap.parse_args()
     if args.workload.startswith("batch") and args.impl == "native":
         return run_batch(args)
+    if args.workload.startswith("sim") and args.impl == "native":
+        return run_sim(args)
     if args.adjoint:
         return run_adjoint(args)
     if args.compare_mixed:

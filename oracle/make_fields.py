@@ -7,6 +7,7 @@ checksum of the locations it belongs to.
 
     python -m oracle.make_fields n16384
     python -m oracle.make_fields batch2048      (the batched-fields workload, 2048 fields)
+    python -m oracle.make_fields sim20          (the simulation study, 20 realisations each)
 """
 import hashlib
 import json
@@ -16,7 +17,7 @@ import time
 
 import numpy as np
 
-from . import fields
+from . import fields, linalg
 
 OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden", "fields")
 
@@ -45,6 +46,31 @@ def write_batch(inputs, count: int, name: str):
     print(meta)
 
 
+def write_sim(inputs, reps: int, name: str):
+    """The simulation-study fields: for every setting and size, z_r = L e_r for r < reps with one
+    oracle factor L of Sigma(theta_true) per (setting, size) on the shared design."""
+    t0 = time.time()
+    zs, h = [], hashlib.sha256()
+    for n in inputs.SIM_SIZES:
+        locs = inputs.sim_locations(n)
+        h.update(np.ascontiguousarray(locs, dtype="<f8").tobytes())
+        for si, th in enumerate(inputs.SIM_SETTINGS):
+            S = fields.covariance_blocked(locs, th, jitter=1e-8, lower_only=True)
+            L = linalg.cholesky(S, nb=256, overwrite=True)
+            for r in range(reps):
+                zs.append(L @ inputs.sim_normals(si, n, r))
+            del S, L
+    np.save(os.path.join(OUT, f"{name}_z.npy"), np.concatenate(zs).astype("<f8"))
+    meta = dict(workload=name, reps=reps, order="for n in SIM_SIZES: for setting: for rep", jitter=1e-8,
+                settings=inputs.SIM_SETTINGS, sizes=inputs.SIM_SIZES, locations_sha256=h.hexdigest(),
+                recipe="paper_2601_11437_gb300.inputs.sim_locations / sim_normals",
+                generator="oracle.fields.covariance_blocked + oracle.linalg.cholesky",
+                command=f"python -m oracle.make_fields {name}", seconds=round(time.time() - t0, 1))
+    with open(os.path.join(OUT, f"{name}_z.json"), "w") as fh:
+        json.dump(meta, fh, indent=1)
+    print(meta)
+
+
 def main(names):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from paper_2601_11437_gb300 import inputs
@@ -52,6 +78,9 @@ def main(names):
     for name in names:
         if name.startswith("batch"):
             write_batch(inputs, int(name[len("batch"):]), name)
+            continue
+        if name.startswith("sim"):
+            write_sim(inputs, int(name[len("sim"):]), name)
             continue
         w = inputs.WORKLOADS[name]
         t0 = time.time()

@@ -124,3 +124,22 @@ def batched_fields(count: int = 2048, seed: int = 4, n_lo: int = 256, n_hi: int 
         th = (0.5 + 1.5 * u[f, 1], 0.02 + 0.28 * u[f, 2], 0.3 + 2.2 * u[f, 3])
         out.append(BatchField(n, seed * 1_000_003 + f, th, (0.7 * th[0], 0.7 * th[1], 0.8 * th[2])))
     return out
+
+
+# Simulation study (Sec. 3): five true parameter settings, three sample sizes, replicated
+# realisations, Fisher-BT started from the L9 design of Table 1 over the box below.
+SIM_SETTINGS = ((1.0, 0.1, 0.5), (0.1, 0.1, 0.1), (0.05, 0.05, 0.05), (2.0, 0.8, 1.0), (1.5, 1.55, 1.3))
+SIM_SIZES = (1600, 3600, 6400)
+SIM_BOX = ((0.01, 0.01, 0.01), (5.0, 5.0, 2.0))
+SIM_SEED = 7
+
+
+def sim_locations(n: int) -> np.ndarray:
+    """The design for sample size n: one seeded set of uniform locations, shared by all
+    settings and realisations (the study varies the realisation, not the design)."""
+    return uniform_locations(n, SIM_SEED * 1_000 + n)
+
+
+def sim_normals(setting: int, n: int, rep: int) -> np.ndarray:
+    """Standard normal vector of realisation rep of (setting, n)."""
+    return standard_normal(n, SIM_SEED * 100_000_000 + setting * 1_000_000 + n * 100 + rep)
