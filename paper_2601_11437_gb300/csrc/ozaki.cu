@@ -64,18 +64,28 @@ __global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ 
     // significant up; a chunk of 128 or more becomes chunk - 256 with a carry into the next, so
     // every digit lies in [-128, 127] (the top one in [0, 128], as F < 2^55); then the sign of x.
     __shared__ int s_exp[32];
+    __shared__ unsigned long long s_part[8][32];
     const int t = blockIdx.x >> 2, rq = (blockIdx.x & 3) * 32;
     const double* X = job.tile_ptr(t, nb);
     unsigned char* out = dst + (size_t)t * (OZ_TILE_BYTES + 128 * sizeof(double));
     int* exp_out = (int*)(out + OZ_TILE_BYTES);
-    if (threadIdx.x < 32) {
-        const int r = rq + threadIdx.x;
+    {   // row maxima: the 8 warps take 16 entries of each of the 32 rows
+        const int rl = threadIdx.x & 31, kq = threadIdx.x >> 5, r = rq + rl;
         unsigned long long mbits = 0;
-        for (int k = 0; k < 128; ++k) {
+#pragma unroll
+        for (int k = kq * 16; k < kq * 16 + 16; ++k) {
             const double v = ROWS ? X[r + k * 128] : X[k + r * 128];
             const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
             mbits = b > mbits ? b : mbits;          // |x| order = integer order of the bits
         }
+        s_part[kq][rl] = mbits;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int r = rq + threadIdx.x;
+        unsigned long long mbits = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mbits = s_part[q][threadIdx.x] > mbits ? s_part[q][threadIdx.x] : mbits;
         const int E = (int)(mbits >> 52);
         const int e = E == 0 ? 0 : E - 1022;        // 2^(e-1) <= max |x| < 2^e (zero row: e = 0)
         s_exp[threadIdx.x] = e;
