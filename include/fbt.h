@@ -195,6 +195,19 @@ fbt_status fisher_bt_run_batch(fbt_ctx* const* ctxs, int nfields, const double* 
                                const double* theta_lo, const double* theta_hi, const fbt_bt_opts* bt,
                                fbt_state* states, int* status, int nthreads);
 
+/*
+ * Graph replay of evaluations (default on).  The launch sequence of an evaluation depends only on
+ * its kind (Algorithm 2 with or without kept partials; Algorithm 3 fresh, reusing the factor,
+ * or reusing factor and partials), not on theta, which reaches the device through a buffer the
+ * sequence itself fills.  The second evaluation of a kind captures its sequence as a CUDA graph;
+ * later ones replay it with one launch.  Results are bitwise those of direct launches.  Not
+ * used for FBT_PREC_MIXED (its plane thresholds depend on sigma^2) or while profiling.
+ * fbt_set_graphs(ctx, 0) switches to direct launches (and drops the captured graphs).
+ */
+fbt_status fbt_set_graphs(fbt_ctx* ctx, int enable);
+/* Number of evaluation kinds currently replayed from a captured graph (0 .. 5). */
+int fbt_graph_count(fbt_ctx* ctx);
+
 /* Per-kernel statistics, recorded with CUDA events on the context's stream while enabled. */
 typedef struct {
     const char* name;     /* kernel family                                                    */

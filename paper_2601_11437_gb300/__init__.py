@@ -295,6 +295,15 @@ def fbt_destroy(ctx: Context) -> None:
         ctx.workspace = None
 
 
+def fbt_set_graphs(ctx: Context, enable: bool) -> None:
+    """Replay evaluations as captured CUDA graphs (default) or launch every kernel directly."""
+    _check(_lib.load().fbt_set_graphs(ctx.handle, 1 if enable else 0), "fbt_set_graphs")
+
+
+def fbt_graph_count(ctx: Context) -> int:
+    return int(_lib.load().fbt_graph_count(ctx.handle))
+
+
 def fbt_profile(ctx: Context, enable: bool) -> None:
     _check(_lib.load().fbt_profile(ctx.handle, int(bool(enable))), "fbt_profile")
 

@@ -57,6 +57,8 @@ SIGNATURES = {
                                        C.POINTER(FbtBtOpts), C.POINTER(C.c_int), C.c_int]),
     "fisher_bt_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, c_double_p, c_double_p,
                                       C.POINTER(FbtBtOpts), C.POINTER(FbtState), C.POINTER(C.c_int), C.c_int]),
+    "fbt_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "fbt_graph_count": (C.c_int, [C.c_void_p]),
     "fbt_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(FbtKernelStat), C.c_int, C.POINTER(C.c_int)]),
     "fbt_launch_count": (C.c_longlong, [C.c_void_p, C.c_int]),

@@ -88,7 +88,7 @@ int launch_adjoint_reduce(Launcher& L, const Geom& g, const double* Xs, const do
     (void)status;
     const long long tiles = num_tiles(g.T);
     const size_t smem = (size_t)(4 * QUAD_LEVELS * QUAD_NODES + 6 * g.nb + EXP_TABLE) * sizeof(double);
-    cudaFuncSetAttribute(k_adjoint_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem((const void*)k_adjoint_reduce, (int)smem);
     L.begin("adjoint_reduce");
     k_adjoint_reduce<<<(unsigned)tiles, 256, smem, L.stream>>>(g, Xs, Yc, X, w, tc, qt, slots);
     L.count();

@@ -4,10 +4,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/fbt.h"
+
 #include "fbt_kernels.cuh"
 #include "fbt_ctx_access.h"
 
@@ -69,6 +72,15 @@ struct Profiler {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
+
+void ensure_smem(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> set;
+    std::lock_guard<std::mutex> lock(mu);
+    int& have = set[kernel];
+    if (have >= bytes) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess) have = bytes;
+}
 
 static thread_local cudaEvent_t tl_start;
 
@@ -133,6 +145,18 @@ struct fbt_ctx {
     bool partials_valid = false;
     double partials_theta[3] = {0.0, 0.0, 0.0};
     long long factor_reuses = 0;
+    // Launch sequences of the evaluation variants (see Variant), captured once as CUDA graphs
+    // and replayed: theta reaches the device through dtheta (copied from pin_theta by the
+    // sequence itself), the result comes back into pin_out.
+    double* dtheta = nullptr;
+    double* pin_theta = nullptr;               // pinned host: sigma^2, alpha, nu, jitter
+    EvalOut* pin_out = nullptr;                // pinned host: the result record
+    bool graphs = true;
+    cudaStream_t cap_stream = nullptr;        // private stream for captures (the caller's may be
+                                              // the legacy default stream, which cannot capture)
+    cudaGraphExec_t gexec[5] = {};
+    long long glaunches[5] = {};
+    int gseen[5] = {};
 };
 
 static thread_local std::string tl_cuda_error;
@@ -171,6 +195,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pperm = take((size_t)n * 8);
     char* pbbox = take(4 * 8);
     char* ptc = take(sizeof(ThetaConsts));
+    char* pth = take(4 * sizeof(double));                  // theta and jitter for prep_theta
     char* pqt = take(sizeof(QuadTables));
     char* pld = take((size_t)T * 8);
     char* pqf = take((size_t)tiles * 2 * 8);
@@ -204,6 +229,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
         c->vy = (double*)pvy; c->vw = (double*)pvw;
         c->perm = (long long*)pperm; c->bbox = (double*)pbbox;
         c->tc = (ThetaConsts*)ptc; c->qt = (QuadTables*)pqt;
+        c->dtheta = (double*)pth;
         c->slots.logdet = (double*)pld; c->slots.qform = (double*)pqf;
         c->slots.diag = (double*)pdg; c->slots.offd = (double*)pod;
         c->status = (int*)pst; c->out = (EvalOut*)pout;
@@ -285,6 +311,16 @@ fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device, con
         c->ws_bytes = need;
     }
     carve(n, o, c->ws, c);
+    {
+        void* pin = nullptr;
+        if (cudaHostAlloc(&pin, 4 * sizeof(double) + sizeof(EvalOut), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            fbt_destroy(c);
+            return FBT_ERR_OOM;
+        }
+        c->pin_theta = (double*)pin;
+        c->pin_out = (EvalOut*)(c->pin_theta + 4);
+    }
     // staging inside the (not yet used) Sigma slab: sort keys, raw locations, raw field
     long long npow2 = 1;
     while (npow2 < n) npow2 <<= 1;
@@ -337,25 +373,116 @@ static bool same_theta(const double a[3], const double b[3]) {
     return a[0] == b[0] && a[1] == b[1] && a[2] == b[2];
 }
 
+// The launch sequence of one evaluation depends only on these flags (and the context), not on
+// theta, so each variant is captured once as a CUDA graph.
+enum Variant : int { V_LOGLIK = 0, V_LOGLIK_KEEP = 1, V_EVAL = 2, V_EVAL_REUSE = 3, V_EVAL_REUSE_PARTIALS = 4 };
+struct EvalFlags {
+    bool deriv, reuse, have_partials, gen_partials;
+    int variant() const {
+        if (!deriv) return gen_partials ? V_LOGLIK_KEEP : V_LOGLIK;
+        if (!reuse) return V_EVAL;
+        return have_partials ? V_EVAL_REUSE_PARTIALS : V_EVAL_REUSE;
+    }
+};
+
+#define EQ(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Enqueue the device work of one evaluation on c->stream (no host synchronisation).
+static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy& pol) {
+    Launcher L = launcher(c);
+    const Geom& g = c->g;
+    int rc = 0;
+    EQ(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
+    EQ(cudaMemcpyAsync(c->dtheta, c->pin_theta, 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy theta");
+    if ((rc = launch_prep_theta_dev(L, c->dtheta, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
+    if (!f.have_partials &&
+        (rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, f.reuse ? nullptr : c->S, c->SA, c->SN, f.gen_partials,
+                              c->status)))
+        return cuda_fail((cudaError_t)rc, "generate");
+    if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol)))
+        return cuda_fail((cudaError_t)rc, "potrf");
+    EQ(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if (f.deriv) {
+        EQ(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+        if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
+        if ((rc = launch_qform(L, g, c->SA, c->SN, c->vw, c->slots.qform))) return cuda_fail((cudaError_t)rc, "qform");
+        // the off-diagonal product slots are indexed by tile; those of diagonal tiles are never
+        // written by the transform and must read as zero in the assembly
+        EQ(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
+           "clear slots");
+        if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd, c->status,
+                               c->opts.precision, c->slices, c->slice_scratch, c->winv, c->wsl,
+                               c->yscratch, pol)))
+            return cuda_fail((cudaError_t)rc, "sygst");
+    }
+    if ((rc = launch_assemble(L, g, c->vy, c->slots, f.deriv, c->tc, c->status, c->out)))
+        return cuda_fail((cudaError_t)rc, "assemble");
+    EQ(cudaMemcpyAsync(c->pin_out, c->out, sizeof(EvalOut), cudaMemcpyDeviceToHost, c->stream), "copy result");
+    return FBT_OK;
+}
+
+// Run one evaluation's device work: directly the first time a variant is seen (and whenever
+// profiling is on or the mixed path bakes a theta-dependent policy into the launches), as a
+// captured graph from then on.  A capture that fails switches the context to direct launches.
+static fbt_status run_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy& pol) {
+    const int v = f.variant();
+    const bool graphable = c->graphs && !c->prof && c->opts.precision != FBT_PREC_MIXED;
+    if (graphable && c->gseen[v] >= 1 && !c->gexec[v]) {
+        const long long before = c->launches;
+        fbt_status est = FBT_OK;
+        cudaGraph_t graph = nullptr;
+        if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            c->cap_stream = nullptr;
+        const cudaStream_t own = c->stream;
+        const cudaError_t eb = c->cap_stream ? cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)
+                                             : cudaErrorInvalidResourceHandle;
+        if (eb == cudaSuccess) {
+            c->stream = c->cap_stream;            // nothing runs while capturing
+            est = enqueue_eval(c, f, pol);
+            c->stream = own;
+            const cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+            const cudaError_t ei = (est == FBT_OK && ee == cudaSuccess && graph)
+                                       ? cudaGraphInstantiate(&c->gexec[v], graph, 0) : cudaErrorUnknown;
+            if (ei == cudaSuccess) {
+                c->glaunches[v] = c->launches - before;
+            } else {
+                tl_cuda_error = std::string("graph capture: ") + cudaGetErrorString(ee != cudaSuccess ? ee : ei);
+                c->gexec[v] = nullptr;
+                c->graphs = false;
+            }
+            if (graph) cudaGraphDestroy(graph);
+        } else {
+            tl_cuda_error = std::string("graph capture: ") + cudaGetErrorString(eb);
+            c->graphs = false;
+        }
+        c->launches = before;
+        cudaGetLastError();
+    }
+    c->gseen[v] += 1;
+    if (graphable && c->graphs && c->gexec[v]) {
+        EQ(cudaGraphLaunch(c->gexec[v], c->stream), "graph launch");
+        c->launches += c->glaunches[v];
+        return FBT_OK;
+    }
+    return enqueue_eval(c, f, pol);
+}
+
 // Shared pipeline of Algorithms 2 and 3.  keep_partials (Algorithm 2 only): generate Sigma_alpha
 // and Sigma_nu together with Sigma (the same exponentials serve all three) and keep them for an
 // Algorithm 3 evaluation at the same theta.
 static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv, bool keep_partials = false) {
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    Launcher L = launcher(c);
-    const Geom& g = c->g;
-    int rc = 0;
-    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "clear status");
     const bool reuse = deriv && c->factor_valid && same_theta(theta, c->factor_theta);
     const bool have_partials = reuse && c->partials_valid && same_theta(theta, c->partials_theta);
     const bool gen_partials = deriv ? !have_partials : (keep_partials && c->opts.with_derivatives);
+    const EvalFlags f{deriv, reuse, have_partials, gen_partials};
     c->factor_valid = false;
     if (deriv || gen_partials) c->partials_valid = false;     // SA, SN are about to change
-    if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
-    if (!have_partials &&
-        (rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, reuse ? nullptr : c->S, c->SA, c->SN, gen_partials,
-                              c->status)))
-        return cuda_fail((cudaError_t)rc, "generate");
     MixedPolicy pol;
     if (c->opts.precision == FBT_PREC_MIXED) {
         // a tile product whose largest possible entry is below tol * sigma^2 * 2^6 may use one
@@ -367,31 +494,15 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv, bool k
         pol.e_fp32 = (int)floor(l2) - 1;
         pol.e_fp64 = (int)floor(l2) + 13;
     }
-    if (reuse) {
-        c->factor_reuses += 1;
-    } else if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol))) {
-        return cuda_fail((cudaError_t)rc, "potrf");
-    }
-    CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
-    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
-    if (deriv) {
-        CK(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
-        if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
-        if ((rc = launch_qform(L, g, c->SA, c->SN, c->vw, c->slots.qform))) return cuda_fail((cudaError_t)rc, "qform");
-        // the off-diagonal product slots are indexed by tile; those of diagonal tiles are never
-        // written by the transform and must read as zero in the assembly
-        CK(cudaMemsetAsync(c->slots.offd, 0, (size_t)num_tiles(g.T) * c->nstrips * 3 * sizeof(double), c->stream),
-           "clear slots");
-        if ((rc = launch_sygst(L, g, c->S, c->SA, c->SN, c->slots.diag, c->slots.offd, c->status,
-                               c->opts.precision, c->slices, c->slice_scratch, c->winv, c->wsl,
-                               c->yscratch, pol)))
-            return cuda_fail((cudaError_t)rc, "sygst");
-    }
-    if ((rc = launch_assemble(L, g, c->vy, c->slots, deriv, c->tc, c->status, c->out)))
-        return cuda_fail((cudaError_t)rc, "assemble");
-    CK(cudaMemcpyAsync(&c->host_out, c->out, sizeof(EvalOut), cudaMemcpyDeviceToHost, c->stream), "copy result");
+    for (int i = 0; i < 3; ++i) c->pin_theta[i] = theta[i];
+    c->pin_theta[3] = c->opts.jitter;
+    if (reuse) c->factor_reuses += 1;
+    fbt_status est = run_eval(c, f, pol);
+    if (est != FBT_OK) return est;
+    c->h2d_bytes += 4 * (long long)sizeof(double);
     c->d2h_bytes += (long long)sizeof(EvalOut);
     CK(cudaStreamSynchronize(c->stream), "evaluation sync");
+    c->host_out = *c->pin_out;
     if (c->prof) c->prof->flush();
     if (c->host_out.status & ST_TIMEOUT) return FBT_ERR_TIMEOUT;
     if (c->host_out.status & ST_NOT_PD) return FBT_ERR_NOT_PD;
@@ -546,6 +657,26 @@ fbt_status fbt_copy_perm(fbt_ctx* c, long long* perm) {
     return FBT_OK;
 }
 
+fbt_status fbt_set_graphs(fbt_ctx* c, int enable) {
+    if (!c) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->stream), "graphs sync");
+    for (int v = 0; v < 5; ++v) {
+        if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
+        c->gexec[v] = nullptr;
+        c->gseen[v] = 0;
+    }
+    c->graphs = enable != 0;
+    return FBT_OK;
+}
+
+int fbt_graph_count(fbt_ctx* c) {
+    if (!c) return 0;
+    int k = 0;
+    for (cudaGraphExec_t x : c->gexec) k += x != nullptr;
+    return k;
+}
+
 fbt_status fbt_profile(fbt_ctx* c, int enable) {
     if (!c) return FBT_ERR_ARG;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -594,6 +725,10 @@ void fbt_destroy(fbt_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (cudaGraphExec_t& x : c->gexec)
+        if (x) cudaGraphExecDestroy(x);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->pin_theta) cudaFreeHost(c->pin_theta);
     delete c->prof;
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;

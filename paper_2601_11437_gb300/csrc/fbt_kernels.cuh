@@ -165,6 +165,10 @@ struct Slots {
     double* offd;       // [ntiles * strips * 3]  <.,.> of off-diagonal tiles (not yet doubled)
 };
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, calling the runtime only when
+// the limit grows (host-side state, kept out of captured launch sequences; thread safe).
+void ensure_smem(const void* kernel, int bytes);
+
 // ---- launch bookkeeping: launch counter and optional CUDA-event timing per kernel family ----
 struct Profiler;
 struct Launcher {
@@ -191,6 +195,8 @@ int launch_permute_field(Launcher& L, const double* z_dev, const long long* perm
 
 int launch_prep_theta(Launcher& L, const double theta[3], double jitter, ThetaConsts* tc,
                       QuadTables* qt);
+// the same from device memory th[4] = (sigma^2, alpha, nu, jitter)
+int launch_prep_theta_dev(Launcher& L, const double* th, ThetaConsts* tc, QuadTables* qt);
 int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y,
                     const ThetaConsts* tc, const QuadTables* qt, double* S, double* SA,
                     double* SN, bool deriv, int* status);

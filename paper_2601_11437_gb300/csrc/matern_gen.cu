@@ -25,8 +25,8 @@ namespace fbt {
 
 __device__ inline double clamp_finite(double v) { return v > 1.0e308 ? 1.0e308 : v; }
 
-__global__ void k_prep_theta(double sigma2, double alpha, double nu, double jitter,
-                             ThetaConsts* __restrict__ tc, QuadTables* __restrict__ qt) {
+__device__ void prep_theta_body(double sigma2, double alpha, double nu, double jitter,
+                                ThetaConsts* __restrict__ tc, QuadTables* __restrict__ qt) {
     const int j = threadIdx.x;
     if (j < EXP_TABLE) qt->exp2tab[j] = exp2(j / (double)EXP_TABLE);
     for (int l = 0; l < QUAD_LEVELS; ++l) {
@@ -48,6 +48,25 @@ __global__ void k_prep_theta(double sigma2, double alpha, double nu, double jitt
         tc->c_nu = 0.69314718055994530942 + digamma_pos(nu);
         tc->jitter = jitter;
     }
+}
+
+__global__ void k_prep_theta(double sigma2, double alpha, double nu, double jitter,
+                             ThetaConsts* __restrict__ tc, QuadTables* __restrict__ qt) {
+    prep_theta_body(sigma2, alpha, nu, jitter, tc, qt);
+}
+
+// theta and the jitter read from device memory (sigma^2, alpha, nu, jitter), so that a captured
+// launch sequence serves every theta
+__global__ void k_prep_theta_dev(const double* __restrict__ th, ThetaConsts* __restrict__ tc,
+                                 QuadTables* __restrict__ qt) {
+    prep_theta_body(th[0], th[1], th[2], th[3], tc, qt);
+}
+
+int launch_prep_theta_dev(Launcher& L, const double* th, ThetaConsts* tc, QuadTables* qt) {
+    L.begin("prep_theta");
+    k_prep_theta_dev<<<1, QUAD_NODES, 0, L.stream>>>(th, tc, qt);
+    L.count();
+    return L.end(0.0, 0.0);
 }
 
 int launch_prep_theta(Launcher& L, const double theta[3], double jitter, ThetaConsts* tc,
@@ -137,10 +156,10 @@ int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y
     const double entries = (double)tiles * g.nb * g.nb;
     L.begin(deriv ? "generate_deriv" : "generate");
     if (deriv) {
-        cudaFuncSetAttribute(k_generate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem((const void*)k_generate<true>, (int)smem);
         k_generate<true><<<(unsigned)tiles, 256, smem, L.stream>>>(g, X, Y, tc, qt, S, SA, SN, status);
     } else {
-        cudaFuncSetAttribute(k_generate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem((const void*)k_generate<false>, (int)smem);
         k_generate<false><<<(unsigned)tiles, 256, smem, L.stream>>>(g, X, Y, tc, qt, S, SA, SN, status);
     }
     L.count();

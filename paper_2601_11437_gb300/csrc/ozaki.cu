@@ -423,7 +423,7 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         return v > 0 ? v : 152;
     }();
-    cudaFuncSetAttribute(k_ozaki_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    ensure_smem((const void*)k_ozaki_gemm, OZ_SMEM);
     const long long grid = ctas < (long long)sms ? ctas : (long long)sms;    // persistent: one CTA per SM
     L.begin(family);
     k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(job, ctas, status);

@@ -343,8 +343,8 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
     const int T = g.T;
     const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
     const size_t smem_trsm1 = (size_t)(STRIP + NB) * (NB + 1) * sizeof(double);
-    cudaFuncSetAttribute(k_potrf_diag<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_potrf);
-    cudaFuncSetAttribute(k_trsm_strip<NB, false, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_trsm1);
+    ensure_smem((const void*)k_potrf_diag<NB>, (int)smem_potrf);
+    ensure_smem((const void*)k_trsm_strip<NB, false, 1, 0>, (int)smem_trsm1);
     constexpr int NS = NB / STRIP;
     constexpr int SB = NB / GB;
     const double nb3 = (double)NB * NB * NB;
@@ -489,7 +489,7 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
     int rc = 0;
     {
         const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
-        cudaFuncSetAttribute(k_trtri_all<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem((const void*)k_trtri_all<NB>, (int)smem);
         L.begin("trtri");
         k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
         L.count();
@@ -589,7 +589,7 @@ int launch_inverse_from_factor(Launcher& L, const Geom& g, const double* S, doub
     unsigned char* Xs = scratch;                                   // up to T sliced tiles
     int rc = 0;
     const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
-    cudaFuncSetAttribute(k_trtri_all<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem((const void*)k_trtri_all<NB>, (int)smem);
     L.begin("trtri");
     k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
     L.count();
@@ -641,9 +641,9 @@ static int sygst_impl(Launcher& L, const Geom& g, const double* S, double* M0, d
     constexpr int NS = NB / STRIP;
     constexpr int SB = NB / GB;
     const size_t smem2 = (size_t)(2 * STRIP + NB) * (NB + 1) * sizeof(double);
-    cudaFuncSetAttribute(k_trsm_strip<NB, false, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    cudaFuncSetAttribute(k_trsm_strip<NB, true, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    ensure_smem((const void*)k_trsm_strip<NB, false, 2, 0>, (int)smem2);
+    ensure_smem((const void*)k_trsm_strip<NB, true, 2, 1>, (int)smem2);
+    ensure_smem((const void*)k_trsm_strip<NB, true, 2, 2>, (int)smem2);
     const double nb3 = (double)NB * NB * NB;
     const double tb = 8.0 * NB * NB;
     int rc = 0;

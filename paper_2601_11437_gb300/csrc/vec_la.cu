@@ -126,8 +126,8 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
     const int T = g.T, nb = g.nb;
     const size_t smem_upd = (size_t)nb * 9 * sizeof(double);
     const size_t smem_diag = (size_t)nb * (nb + 2) * sizeof(double);
-    cudaFuncSetAttribute(k_trsv_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
-    cudaFuncSetAttribute(k_trsv_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_diag);
+    ensure_smem((const void*)k_trsv_diag<false>, (int)smem_diag);
+    ensure_smem((const void*)k_trsv_diag<true>, (int)smem_diag);
     const double tb = 8.0 * nb * nb;
     int rc = 0;
     L.begin(trans ? "trsv_backward" : "trsv_forward");

@@ -263,3 +263,28 @@ def test_line_search_partials_are_kept_for_the_accepted_point(precision):
     fbt.mle_loglik(a, (0.7, 0.07, 0.9))
     e = fbt.mle_eval(a, th)
     assert e[0] == ll and np.array_equal(e[1], g)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
+def test_graph_replay_is_bitwise_the_direct_path(precision):
+    # every evaluation kind, several times: the first runs directly, the second is captured, the
+    # rest replay the graph; a context with graphs off must give the same bits throughout
+    import paper_2601_11437_gb300 as fbt
+    locs, z = field(420, 23, (1.0, 0.1, 0.9))
+    a = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    b = fbt.fbt_create(locs, z, nb=128, precision=precision)
+    fbt.fbt_set_graphs(b, False)
+    for ctx in (a, b):
+        ctx.trace = []
+    thetas = [(0.9, 0.08, 1.1), (1.1, 0.12, 0.8), (0.7, 0.05, 1.4)]
+    for rep in range(3):
+        for th in thetas:
+            for ctx in (a, b):
+                ctx.trace.append(fbt.mle_loglik(ctx, th))                 # Algorithm 2
+                ll, g, I = fbt.mle_eval(ctx, th)                           # reuses the factor
+                ctx.trace += [ll, *g, *I.ravel()]
+                st = fbt.fisher_bt_start(ctx, th)                          # fresh eval + step machinery
+                fbt.fisher_bt_step(ctx, st)                                # kept partials path
+                ctx.trace += [st.loglik, *st.theta[:], *st.score[:]]
+    assert a.trace == b.trace
+    assert fbt.fbt_graph_count(a) >= 3 and fbt.fbt_graph_count(b) == 0, fbt._lib.load().fbt_last_cuda_error()
