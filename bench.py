@@ -267,8 +267,8 @@ def run_native(args):
         roof = {"bound": "alu", "kernel": f"k_gemm_tile ({dom})", "achieved": fp64eq, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": fp64eq / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 DFMA pipe)"}
-    chol = {k: prof[k] for k in ("potrf_diag", "trsm_panel", "gemm_potrf_update", "ozaki_potrf_update",
-                                 "ozaki_slice") if k in prof}
+    chol = {k: prof[k] for k in ("potrf_diag", "trsm_panel", "trtri_panel", "ozaki_potrf_panel",
+                                 "gemm_potrf_update", "ozaki_potrf_update", "ozaki_slice") if k in prof}
     chol_tf = sum(v["flops"] for v in chol.values()) / (sum(v["ms"] for v in chol.values()) * 1e-3) / 1e12
     total_ms = sum(v["ms"] for v in prof.values())
 
@@ -494,7 +494,8 @@ def run_compare(args):
         torch.cuda.synchronize()
         prof = fbt.fbt_profile_read(ctx)
         fbt.fbt_profile(ctx, False)
-        chol = {k: v for k, v in prof.items() if k in ("potrf_diag", "trsm_panel", "ozaki_potrf_update", "ozaki_slice")}
+        chol = {k: v for k, v in prof.items() if k in ("potrf_diag", "trsm_panel", "trtri_panel", "ozaki_potrf_panel",
+                                                       "ozaki_potrf_update", "ozaki_slice")}
         # the slicing of the Cholesky's panels is counted with the Cholesky (the transforms' slices are not)
         chol_ms = sum(v["ms"] for k, v in chol.items() if k != "ozaki_slice")
         n = w.n

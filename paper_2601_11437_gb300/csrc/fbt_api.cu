@@ -403,7 +403,7 @@ static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy
         (rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, f.reuse ? nullptr : c->S, c->SA, c->SN, f.gen_partials,
                               c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
-    if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol)))
+    if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl)))
         return cuda_fail((cudaError_t)rc, "potrf");
     EQ(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
     if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
@@ -539,7 +539,7 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
     } else {
         if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, nullptr, nullptr, false, c->status)))
             return cuda_fail((cudaError_t)rc, "generate");
-        if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol)))
+        if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl)))
             return cuda_fail((cudaError_t)rc, "potrf");
     }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");

@@ -207,10 +207,12 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
                       const char* family);
 
 // tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile;
-// precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`)
+// precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`), and with
+// `wtiles` / `wslices` (T FP64 tiles, T sliced tiles of scratch) the panel solves as well
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
                  int precision = PREC_FP64, unsigned char* slices = nullptr,
-                 const MixedPolicy& pol = MixedPolicy());
+                 const MixedPolicy& pol = MixedPolicy(), double* wtiles = nullptr,
+                 unsigned char* wslices = nullptr);
 // two-sided transform B = L^-1 M L^-T of both derivative slabs in place, with the trace and
 // Frobenius-product partials of the result
 // precision PREC_FP64_OZAKI: L_slices holds the digit planes of every strictly-lower tile of L

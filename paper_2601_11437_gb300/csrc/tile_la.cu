@@ -337,9 +337,60 @@ static inline OzGemmJob with_policy(OzGemmJob j, const MixedPolicy& pol) {
     j.e_fp32 = pol.e_fp32;
     return j;
 }
+// W = L_kk^-1 by columns: warp c of the launch solves L w = e_c by forward substitution with the
+// vector in registers (as the diagonal TRSV does), so one tile's inverse spreads over NB / 8
+// CTAs instead of running column after column in one.  The factor tile is staged in shared memory.
+template <int NB>
+__global__ void __launch_bounds__(256) k_trtri_cols(const double* __restrict__ S, int T, int k,
+                                                   double* __restrict__ W) {
+    extern __shared__ double A[];
+    constexpr int LD = NB + 1;
+    constexpr int NBLK = NB / 32;
+    double* rinv = A + NB * LD;
+    const double* __restrict__ Lt = S + tile_offset(k, k, T, NB);
+    {
+        const double2* __restrict__ L2 = (const double2*)Lt;
+#pragma unroll 16
+        for (int e2 = threadIdx.x; e2 < NB * NB / 2; e2 += blockDim.x) {
+            const double2 w = L2[e2];
+            const int r = (2 * e2) % NB, c = (2 * e2) / NB;
+            if (r >= c) A[r + c * LD] = w.x;
+            if (r + 1 >= c) A[r + 1 + c * LD] = w.y;
+        }
+    }
+    for (int d = threadIdx.x; d < NB; d += blockDim.x) rinv[d] = 1.0 / Lt[d + (long long)d * NB];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    double x[NBLK];
+#pragma unroll
+    for (int s = 0; s < NBLK; ++s) x[s] = lane + 32 * s == c ? 1.0 : 0.0;
+#pragma unroll
+    for (int s = 0; s < NBLK; ++s) {
+        for (int dd = 0; dd < 32; ++dd) {
+            const int d = 32 * s + dd;
+            if (d < c) continue;                        // warp-uniform
+            double xd = 0.0;
+            if (lane == dd) { xd = x[s] * rinv[d]; x[s] = xd; }
+            xd = __shfl_sync(0xffffffffu, xd, dd);
+#pragma unroll
+            for (int t = 0; t < NBLK; ++t) {
+                const int r = lane + 32 * t;
+                if (t >= s && r > d) x[t] -= A[r + d * LD] * xd;
+            }
+        }
+    }
+    double* Wc = W + (long long)c * NB;
+#pragma unroll
+    for (int s = 0; s < NBLK; ++s) {
+        const int r = lane + 32 * s;
+        Wc[r] = r >= c ? x[s] : 0.0;
+    }
+}
+
 template <int NB>
 static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
-                      int precision, unsigned char* slices, const MixedPolicy& pol) {
+                      int precision, unsigned char* slices, const MixedPolicy& pol, double* wtiles,
+                      unsigned char* wslices) {
     const int T = g.T;
     const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
     const size_t smem_trsm1 = (size_t)(STRIP + NB) * (NB + 1) * sizeof(double);
@@ -356,15 +407,37 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
         if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
         const int m = T - k - 1;
         if (m == 0) break;
-        TrsmParams tp{TRSM_POTRF_PANEL, k, T, S, nullptr, nullptr, nullptr};
-        L.begin("trsm_panel");
-        k_trsm_strip<NB, false, 1, 0><<<m * NS, 256, smem_trsm1, L.stream>>>(tp);
-        L.count();
-        if ((rc = L.end((double)m * nb3, 16.0 * m * NB * NB))) return rc;
+        const bool tensor = NB == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED);
+        if (tensor && wtiles && wslices) {
+            // panel on tensor cores: W_k = L_kk^-1 (column-parallel), then L_ik = A_ik W_k^T as an
+            // FP64-accurate tile product (all digit planes), instead of FP64 strip solves
+            const size_t tb = ozaki_tile_bytes();
+            double* Wk = wtiles + (size_t)k * NB * NB;
+            unsigned char* Wks = wslices + (size_t)k * tb;
+            unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * tb;
+            const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
+            ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
+            L.begin("trtri_panel");
+            k_trtri_cols<NB><<<NB / 8, 256, smem_tc, L.stream>>>(S, T, k, Wk);
+            L.count();
+            if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
+            SliceJob wj{Wk, SLICE_PTR, 0, T};
+            if ((rc = launch_ozaki_slice(L, g, wj, 1, true, Wks))) return rc;
+            SliceJob aj{S, SLICE_PANEL, k, T};
+            if ((rc = launch_ozaki_slice(L, g, aj, m, true, panel))) return rc;   // digits of A_ik
+            OzGemmJob pj{OZ_SYGST_FIX, k, T, S, panel, Wks, tb, -1.0, 1};
+            if ((rc = launch_ozaki_gemm(L, pj, (long long)m * 2, m * 2.0 * nb3, status, "ozaki_potrf_panel"))) return rc;
+        } else {
+            TrsmParams tp{TRSM_POTRF_PANEL, k, T, S, nullptr, nullptr, nullptr};
+            L.begin("trsm_panel");
+            k_trsm_strip<NB, false, 1, 0><<<m * NS, 256, smem_trsm1, L.stream>>>(tp);
+            L.count();
+            if ((rc = L.end((double)m * nb3, 16.0 * m * NB * NB))) return rc;
+        }
         const long long tasks = (long long)m * (m + 1) / 2;
         // algorithmic flops: 2 nb^3 per off-diagonal tile, nb^3 + nb^2 for a diagonal (SYRK) tile
         const double fl = (double)m * (m - 1) / 2 * 2.0 * nb3 + m * (nb3 + (double)NB * NB);
-        if (NB == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED)) {
+        if (tensor) {
             // digit planes of panel k, kept for the two-sided transforms
             unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * ozaki_tile_bytes();
             SliceJob sj{S, SLICE_PANEL, k, T};
@@ -383,9 +456,10 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
 }
 
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
-                 int precision, unsigned char* slices, const MixedPolicy& pol) {
-    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices, pol);
-    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices, pol);
+                 int precision, unsigned char* slices, const MixedPolicy& pol, double* wtiles,
+                 unsigned char* wslices) {
+    if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
+    if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
     return cudaErrorInvalidValue;
 }
 
