@@ -203,13 +203,14 @@ __device__ inline double fx_to_double(long long fx, int s) {
 }
 
 // Persistent (one CTA per SM), warp-specialised: warp 0 issues the MMAs, warp 1 streams digit
-// stages with bulk copies (4-stage ring), warps 2..9 drain the TMEM accumulators (warp w reads
-// TMEM lanes 32 (w % 4) .. +31, columns 32 ((w - 2) / 4) .. +31).  The accumulators are released
+// stages with bulk copies (4-stage ring), warps 2..17 drain the TMEM accumulators (warp w reads
+// TMEM lanes 32 (w % 4) .. +31, columns 16 ((w - 2) / 4) .. +15).  The accumulators are released
 // as soon as they are folded into 64-bit fixed point in registers, so the next task's MMAs run
-// while the epilogue converts and updates C in FP64.  N = 64 because an M = 128 MMA costs the
-// same issue time for any N <= 64 (measured on GB300), and TMEM holds 8 groups x 64 columns.
-constexpr int OZ_THREADS = 320;
-constexpr int OZ_EPI_WARPS = 8;
+// while the epilogue converts and updates C in FP64; the drain is on the critical path between
+// tasks, hence 16 epilogue warps.  N = 64 per task because TMEM holds the 7 groups x 64 columns.
+constexpr int OZ_EPI_WARPS = 16;                        // 4 per TMEM lane quarter
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+constexpr int OZ_EPI_COLS = OZ_N * 4 / OZ_EPI_WARPS;   // accumulator columns per epilogue warp
 
 // Digit planes used for a task: 8 (FP64-accurate); in the mixed path 3 or 1 when the operand
 // tiles' largest entries, 2^ea and 2^eb, make the product small against the thresholds.
@@ -318,10 +319,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
             }
         }
     } else {
-        // epilogue warps 2..9: rows of TMEM lane quarter w % 4, columns 32 ((w - 2) / 4) .. +31
+        // epilogue warps 2..: rows of TMEM lane quarter w % 4, columns OZ_EPI_COLS ((w - 2) / 4) ..
         const int quarter = warp & 3;
         const int r = quarter * 32 + lane;
-        const int chalf = ((warp - 2) >> 2) * 32;
+        const int chalf = ((warp - 2) >> 2) * OZ_EPI_COLS;
         long long nt = 0;
         for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
             const unsigned char *sa, *sb;
@@ -332,9 +333,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
             const int np = task_planes(job, sa, sb);
             if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            long long fx[32];
+            long long fx[OZ_EPI_COLS];
 #pragma unroll
-            for (int cb = 0; cb < 32; cb += 8) {
+            for (int cb = 0; cb < OZ_EPI_COLS; cb += 8) {
                 uint32_t v[OZ_G][8];
 #pragma unroll
                 for (int g = 0; g < OZ_G; ++g)
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
             double* __restrict__ Cr = C + r + (long long)(c0 + chalf) * 128;
             // C values are loaded 16 at a time before any is stored, so their latencies overlap
 #pragma unroll
-            for (int h = 0; h < 32; h += 16) {
+            for (int h = 0; h < OZ_EPI_COLS; h += 16) {
                 double cv[16];
                 int eb[16];
 #pragma unroll
