@@ -205,6 +205,9 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
                        unsigned char* dst);
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
                       const char* family);
+// up to 4 jobs (tasks[j] tasks each, targets that do not overlap) in one persistent launch
+int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* tasks, int njobs, double flops,
+                            int* status, const char* family);
 
 // tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile;
 // precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`), and with

@@ -224,7 +224,21 @@ __device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa,
     return e >= job.e_fp64 ? OZ_S : (e >= job.e_fp32 ? 3 : 1);
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, long long ntasks, int* status) {
+// Up to four jobs run as one task list (their targets must not overlap): task t belongs to the
+// first job whose cumulative end exceeds t.
+struct OzJobList {
+    OzGemmJob job[4];
+    long long end[4];
+    int n;
+    __device__ const OzGemmJob& pick(long long t, long long& local) const {
+        int j = 0;
+        while (j + 1 < n && t >= end[j]) ++j;
+        local = t - (j ? end[j - 1] : 0);
+        return job[j];
+    }
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, long long ntasks, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
     unsigned char* stA = oz_smem;                                    // [4][32 KB]
     unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [4][16 KB]
@@ -263,7 +277,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                 double* C;
                 int c0;
                 double mult;
-                job.task(t, sa, sb, C, c0, mult);
+                long long lt;
+                const OzGemmJob& job = jobs.pick(t, lt);
+                job.task(lt, sa, sb, C, c0, mult);
                 const int np = task_planes(job, sa, sb);
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
@@ -294,7 +310,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
                 double* Cq;
                 int cq;
                 double mq;
-                job.task(t, sa, sb, Cq, cq, mq);
+                long long lt;
+                const OzGemmJob& job = jobs.pick(t, lt);
+                job.task(lt, sa, sb, Cq, cq, mq);
                 const int np = task_planes(job, sa, sb);
                 if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1))) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -329,7 +347,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzGemmJob job, lon
             double* C;
             int c0;
             double mult;
-            job.task(t, sa, sb, C, c0, mult);
+            long long lt;
+            const OzGemmJob& job = jobs.pick(t, lt);
+            job.task(lt, sa, sb, C, c0, mult);
             const int np = task_planes(job, sa, sb);
             if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -417,6 +437,20 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
 
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
                       const char* family) {
+    return launch_ozaki_gemm_multi(L, &job, &ctas, 1, flops, status, family);
+}
+
+int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* tasks, int njobs, double flops,
+                            int* status, const char* family) {
+    if (njobs < 1 || njobs > 4) return cudaErrorInvalidValue;
+    OzJobList jl{};
+    long long ctas = 0;
+    for (int j = 0; j < njobs; ++j) {
+        jl.job[j] = job[j];
+        ctas += tasks[j];
+        jl.end[j] = ctas;
+    }
+    jl.n = njobs;
     if (ctas <= 0) return 0;
     static const int sms = [] {          // initialised once, also when several host threads launch
         int dev = 0, v = 0;
@@ -427,7 +461,7 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
     ensure_smem((const void*)k_ozaki_gemm, OZ_SMEM);
     const long long grid = ctas < (long long)sms ? ctas : (long long)sms;    // persistent: one CTA per SM
     L.begin(family);
-    k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(job, ctas, status);
+    k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
     L.count();
     return L.end(flops, 0.0);
 }

@@ -572,49 +572,58 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         if ((rc = launch_ozaki_slice(L, g, wj, T, true, Wsl))) return rc;
     }
     const double tile_fl = 2.0 * nb3;
+    // the two matrices' products of each step share one launch (their targets are disjoint)
+    auto both = [&](const OzGemmJob& j0, const OzGemmJob& j1, long long tasks, double fl, const char* fam) {
+        const OzGemmJob js[2] = {with_policy(j0, pol), with_policy(j1, pol)};
+        const long long ts[2] = {tasks, tasks};
+        return launch_ozaki_gemm_multi(L, js, ts, 2, 2.0 * fl, status, fam);
+    };
     for (int k = 0; k < T; ++k) {
         const unsigned char* Wk = Wsl + (size_t)k * tb;
         // B_kk = W_k M_kk W_k^T: Y = M_kk W_k^T, then B_kk = W_k Y
         for (int q = 0; q < 2; ++q) {
             SliceJob dj{M[q], SLICE_DIAG, k, T};
             if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
-            OzGemmJob y = with_policy({OZ_SINGLE, k, T, Ys[q], Ds[q], Wk, tb, -1.0, 1}, pol);
-            if ((rc = launch_ozaki_gemm(L, y, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
+        }
+        if ((rc = both({OZ_SINGLE, k, T, Ys[0], Ds[0], Wk, tb, -1.0, 1}, {OZ_SINGLE, k, T, Ys[1], Ds[1], Wk, tb, -1.0, 1},
+                       2, tile_fl, "ozaki_sygst_solve"))) return rc;
+        for (int q = 0; q < 2; ++q) {
             SliceJob zj{Ys[q], SLICE_PTR, 0, T};
             if ((rc = launch_ozaki_slice(L, g, zj, 1, false, Zs[q]))) return rc;
-            OzGemmJob b = with_policy({OZ_SINGLE, k, T, M[q] + tile_offset(k, k, T, NB), Wk, Zs[q], tb, -1.0, 1}, pol);
-            if ((rc = launch_ozaki_gemm(L, b, 2, tile_fl, status, "ozaki_sygst_solve"))) return rc;
         }
+        if ((rc = both({OZ_SINGLE, k, T, M[0] + tile_offset(k, k, T, NB), Wk, Zs[0], tb, -1.0, 1},
+                       {OZ_SINGLE, k, T, M[1] + tile_offset(k, k, T, NB), Wk, Zs[1], tb, -1.0, 1},
+                       2, tile_fl, "ozaki_sygst_solve"))) return rc;
         const int m = T - k - 1;
         if (m == 0) break;
         const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
-        for (int q = 0; q < 2; ++q) {      // C_ik = M_ik W_k^T, then the digit planes of B_kk
+        // C_ik = M_ik W_k^T, then the digit planes of B_kk
+        for (int q = 0; q < 2; ++q) {
             SliceJob pj{M[q], SLICE_PANEL, k, T};
             if ((rc = launch_ozaki_slice(L, g, pj, m, true, Xs[q]))) return rc;
-            OzGemmJob c = with_policy({OZ_SYGST_FIX, k, T, M[q], Xs[q], Wk, tb, -1.0, 1}, pol);
-            if ((rc = launch_ozaki_gemm(L, c, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
+        }
+        if ((rc = both({OZ_SYGST_FIX, k, T, M[0], Xs[0], Wk, tb, -1.0, 1}, {OZ_SYGST_FIX, k, T, M[1], Xs[1], Wk, tb, -1.0, 1},
+                       (long long)m * 2, m * tile_fl, "ozaki_sygst_solve"))) return rc;
+        for (int q = 0; q < 2; ++q) {
             SliceJob dj{M[q], SLICE_DIAG, k, T};
             if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
         }
-        for (int q = 0; q < 2; ++q) {      // E_ik = C_ik - 1/2 L_ik B_kk
-            OzGemmJob j = with_policy({OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0}, pol);
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
-        }
+        // E_ik = C_ik - 1/2 L_ik B_kk
+        if ((rc = both({OZ_SYGST_FIX, k, T, M[0], Lp, Ds[0], tb, 0.5, 0}, {OZ_SYGST_FIX, k, T, M[1], Lp, Ds[1], tb, 0.5, 0},
+                       (long long)m * 2, m * tile_fl, "ozaki_sygst_fix"))) return rc;
         for (int q = 0; q < 2; ++q) {
             SliceJob ej{M[q], SLICE_PANEL, k, T};
             if ((rc = launch_ozaki_slice(L, g, ej, m, true, Xs[q]))) return rc;
         }
         const long long tasks = (long long)m * (m + 1) / 2;
-        for (int q = 0; q < 2; ++q) {      // M_ij -= L_ik E_jk^T + E_ik L_jk^T
-            OzGemmJob t1 = with_policy({OZ_SYGST_UPD, k, T, M[q], Lp, Xs[q], tb, 1.0, 0}, pol);
-            if ((rc = launch_ozaki_gemm(L, t1, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
-            OzGemmJob t2 = with_policy({OZ_SYGST_UPD, k, T, M[q], Xs[q], Lp, tb, 1.0, 0}, pol);
-            if ((rc = launch_ozaki_gemm(L, t2, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_update"))) return rc;
-        }
-        for (int q = 0; q < 2; ++q) {      // P_ik = E_ik - 1/2 L_ik B_kk
-            OzGemmJob j = with_policy({OZ_SYGST_FIX, k, T, M[q], Lp, Ds[q], tb, 0.5, 0}, pol);
-            if ((rc = launch_ozaki_gemm(L, j, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_fix"))) return rc;
-        }
+        // M_ij -= L_ik E_jk^T + E_ik L_jk^T (the two terms of one target in separate launches)
+        if ((rc = both({OZ_SYGST_UPD, k, T, M[0], Lp, Xs[0], tb, 1.0, 0}, {OZ_SYGST_UPD, k, T, M[1], Lp, Xs[1], tb, 1.0, 0},
+                       tasks * 2, tasks * tile_fl, "ozaki_sygst_update"))) return rc;
+        if ((rc = both({OZ_SYGST_UPD, k, T, M[0], Xs[0], Lp, tb, 1.0, 0}, {OZ_SYGST_UPD, k, T, M[1], Xs[1], Lp, tb, 1.0, 0},
+                       tasks * 2, tasks * tile_fl, "ozaki_sygst_update"))) return rc;
+        // P_ik = E_ik - 1/2 L_ik B_kk
+        if ((rc = both({OZ_SYGST_FIX, k, T, M[0], Lp, Ds[0], tb, 0.5, 0}, {OZ_SYGST_FIX, k, T, M[1], Lp, Ds[1], tb, 0.5, 0},
+                       (long long)m * 2, m * tile_fl, "ozaki_sygst_fix"))) return rc;
     }
     // B_(m,kk) = W_m (P_(m,kk) - sum_(kk<p<m) L_mp B_(p,kk)), row by row
     for (int m = 1; m < T; ++m) {
@@ -622,9 +631,9 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         for (int q = 0; q < 2; ++q) {
             SliceJob rj{M[q], SLICE_ROW, m, T};
             if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
-            OzGemmJob r = with_policy({OZ_ROWSOLVE, m, T, M[q], Wm, Xs[q], tb, -1.0, 1}, pol);
-            if ((rc = launch_ozaki_gemm(L, r, (long long)m * 2, m * tile_fl, status, "ozaki_sygst_solve"))) return rc;
         }
+        if ((rc = both({OZ_ROWSOLVE, m, T, M[0], Wm, Xs[0], tb, -1.0, 1}, {OZ_ROWSOLVE, m, T, M[1], Wm, Xs[1], tb, -1.0, 1},
+                       (long long)m * 2, m * tile_fl, "ozaki_sygst_solve"))) return rc;
         const int below = T - m - 1;
         if (below == 0) continue;
         const unsigned char* Lp = LS + strict_lower_pos(m + 1, m, T) * tb;
@@ -633,10 +642,9 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
             if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
         }
         const long long tasks = (long long)below * m;
-        for (int q = 0; q < 2; ++q) {      // M_(i,kk) -= L_(i,m) M_(m,kk)
-            OzGemmJob j = with_policy({OZ_SYGST_ROWUPD, m, T, M[q], Lp, Xs[q], tb, 1.0, 0}, pol);
-            if ((rc = launch_ozaki_gemm(L, j, tasks * 2, tasks * tile_fl, status, "ozaki_sygst_rowupd"))) return rc;
-        }
+        // M_(i,kk) -= L_(i,m) M_(m,kk)
+        if ((rc = both({OZ_SYGST_ROWUPD, m, T, M[0], Lp, Xs[0], tb, 1.0, 0}, {OZ_SYGST_ROWUPD, m, T, M[1], Lp, Xs[1], tb, 1.0, 0},
+                       tasks * 2, tasks * tile_fl, "ozaki_sygst_rowupd"))) return rc;
     }
     L.begin("frob_epilogue");
     k_frob_tiles<<<(unsigned)num_tiles(T), 256, 0, L.stream>>>(g, M0, M1, strips_per_tile(NB), diag_slots, offd_slots);
