@@ -203,6 +203,9 @@ int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y
 
 int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntiles, bool rows,
                        unsigned char* dst);
+// the same tiles of two jobs (ntiles each) in one launch
+int launch_ozaki_slice2(Launcher& L, const Geom& g, const SliceJob& job0, unsigned char* dst0,
+                        const SliceJob& job1, unsigned char* dst1, int ntiles, bool rows);
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,
                       const char* family);
 // up to 4 jobs (tasks[j] tasks each, targets that do not overlap) in one persistent launch

@@ -32,13 +32,14 @@ static __device__ double digamma_pos(double x) {
     return acc + log(x) - 0.5 / x - s;
 }
 
-// e^a for a <= 0 by table-driven argument reduction (P. T. P. Tang, "Table-driven implementation
+// e^a for a <= 700 by table-driven argument reduction (P. T. P. Tang, "Table-driven implementation
 // of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
 // a = (256 m + j) ln2/256 + r with |r| <= ln2/512, e^a = 2^m 2^(j/256) e^r, e^r - 1 by its
 // degree-4 Taylor polynomial (truncation below 4e-17 relative, odd in r), ln2/256 split into a
 // 35-bit head (n * head is exact for |n| < 2^18) and a tail, 2^m applied to the exponent field.
 __device__ __forceinline__ double exp_nonpos(double a, const double* __restrict__ tab) {
     if (a < -700.0) return 0.0;                                 // keeps 2^m y a normal number
+                                                                // (a <= 700: no overflow either)
     const double n = rint(a * 369.3299304675746);              // 256 / ln 2
     double r = fma(-n, 0x1.62e42fefc0000p-9, a);               // ln 2 / 256, head
     r = fma(-n, -0x1.c610ca86c3899p-45, r);                     // ln 2 / 256, tail
@@ -84,7 +85,8 @@ __device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& t
         if (done) break;
     }
     const double lx = log(x);
-    const double P = tc.norm * exp(tc.nu * lx - x);      // x^nu e^-x / (2^(nu-1) Gamma(nu))
+    // x^nu e^-x / (2^(nu-1) Gamma(nu)); nu log x - x <= nu (log nu - 1) stays far below 700
+    const double P = tc.norm * exp_nonpos(tc.nu * lx - x, etab);
     v.r = P * sa;
     if (DERIV) {
         v.da = P * x * sb * tc.inv_alpha;

@@ -57,15 +57,19 @@ __host__ __device__ inline uint32_t oz_off(int p, int row, int k) {
 //   ROWS = false: operand rows = tile columns, K = tile rows  (B = X in C -= A X)
 // ------------------------------------------------------------------------------------------
 template <bool ROWS>
-__global__ void __launch_bounds__(256) k_ozaki_slice(const double* __restrict__ S, int T, int nb,
-                                                     SliceJob job, unsigned char* __restrict__ dst) {
+__global__ void __launch_bounds__(256) k_ozaki_slice(int nb, SliceJob job0, unsigned char* __restrict__ dst0,
+                                                     SliceJob job1, unsigned char* __restrict__ dst1, int n0) {
     // 4 CTAs per tile, 32 operand rows each; the digits are taken from the FP64 bit fields:
     // F = floor(|x| 2^(55 - E_r)) < 2^55 (exact), cut into 8-bit chunks from the least
     // significant up; a chunk of 128 or more becomes chunk - 256 with a carry into the next, so
     // every digit lies in [-128, 127] (the top one in [0, 128], as F < 2^55); then the sign of x.
     __shared__ int s_exp[32];
     __shared__ unsigned long long s_part[8][32];
-    const int t = blockIdx.x >> 2, rq = (blockIdx.x & 3) * 32;
+    // tiles [0, n0) of the launch come from job0, the rest from job1 (two matrices in one launch)
+    const bool second = (int)(blockIdx.x >> 2) >= n0;
+    const SliceJob& job = second ? job1 : job0;
+    unsigned char* __restrict__ dst = second ? dst1 : dst0;
+    const int t = (int)(blockIdx.x >> 2) - (second ? n0 : 0), rq = (blockIdx.x & 3) * 32;
     const double* X = job.tile_ptr(t, nb);
     unsigned char* out = dst + (size_t)t * (OZ_TILE_BYTES + 128 * sizeof(double));
     int* exp_out = (int*)(out + OZ_TILE_BYTES);
@@ -429,10 +433,20 @@ int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntil
                        unsigned char* dst) {
     if (ntiles <= 0) return 0;
     L.begin("ozaki_slice");
-    if (rows) k_ozaki_slice<true><<<ntiles * 4, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
-    else k_ozaki_slice<false><<<ntiles * 4, 256, 0, L.stream>>>(job.src, g.T, g.nb, job, dst);
+    if (rows) k_ozaki_slice<true><<<ntiles * 4, 256, 0, L.stream>>>(g.nb, job, dst, job, dst, ntiles);
+    else k_ozaki_slice<false><<<ntiles * 4, 256, 0, L.stream>>>(g.nb, job, dst, job, dst, ntiles);
     L.count();
     return L.end(0.0, (double)ntiles * (128.0 * 128 * 8 + OZ_TILE_BYTES));
+}
+
+int launch_ozaki_slice2(Launcher& L, const Geom& g, const SliceJob& job0, unsigned char* dst0,
+                        const SliceJob& job1, unsigned char* dst1, int ntiles, bool rows) {
+    if (ntiles <= 0) return 0;
+    L.begin("ozaki_slice");
+    if (rows) k_ozaki_slice<true><<<ntiles * 8, 256, 0, L.stream>>>(g.nb, job0, dst0, job1, dst1, ntiles);
+    else k_ozaki_slice<false><<<ntiles * 8, 256, 0, L.stream>>>(g.nb, job0, dst0, job1, dst1, ntiles);
+    L.count();
+    return L.end(0.0, 2.0 * ntiles * (128.0 * 128 * 8 + OZ_TILE_BYTES));
 }
 
 int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double flops, int* status,

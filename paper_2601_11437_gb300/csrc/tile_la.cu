@@ -581,16 +581,12 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
     for (int k = 0; k < T; ++k) {
         const unsigned char* Wk = Wsl + (size_t)k * tb;
         // B_kk = W_k M_kk W_k^T: Y = M_kk W_k^T, then B_kk = W_k Y
-        for (int q = 0; q < 2; ++q) {
-            SliceJob dj{M[q], SLICE_DIAG, k, T};
-            if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_DIAG, k, T}, Ds[0],
+                                      SliceJob{M[1], SLICE_DIAG, k, T}, Ds[1], 1, true))) return rc;
         if ((rc = both({OZ_SINGLE, k, T, Ys[0], Ds[0], Wk, tb, -1.0, 1}, {OZ_SINGLE, k, T, Ys[1], Ds[1], Wk, tb, -1.0, 1},
                        2, tile_fl, "ozaki_sygst_solve"))) return rc;
-        for (int q = 0; q < 2; ++q) {
-            SliceJob zj{Ys[q], SLICE_PTR, 0, T};
-            if ((rc = launch_ozaki_slice(L, g, zj, 1, false, Zs[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{Ys[0], SLICE_PTR, 0, T}, Zs[0],
+                                      SliceJob{Ys[1], SLICE_PTR, 0, T}, Zs[1], 1, false))) return rc;
         if ((rc = both({OZ_SINGLE, k, T, M[0] + tile_offset(k, k, T, NB), Wk, Zs[0], tb, -1.0, 1},
                        {OZ_SINGLE, k, T, M[1] + tile_offset(k, k, T, NB), Wk, Zs[1], tb, -1.0, 1},
                        2, tile_fl, "ozaki_sygst_solve"))) return rc;
@@ -598,23 +594,17 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
         if (m == 0) break;
         const unsigned char* Lp = LS + strict_lower_pos(k + 1, k, T) * tb;
         // C_ik = M_ik W_k^T, then the digit planes of B_kk
-        for (int q = 0; q < 2; ++q) {
-            SliceJob pj{M[q], SLICE_PANEL, k, T};
-            if ((rc = launch_ozaki_slice(L, g, pj, m, true, Xs[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_PANEL, k, T}, Xs[0],
+                                      SliceJob{M[1], SLICE_PANEL, k, T}, Xs[1], m, true))) return rc;
         if ((rc = both({OZ_SYGST_FIX, k, T, M[0], Xs[0], Wk, tb, -1.0, 1}, {OZ_SYGST_FIX, k, T, M[1], Xs[1], Wk, tb, -1.0, 1},
                        (long long)m * 2, m * tile_fl, "ozaki_sygst_solve"))) return rc;
-        for (int q = 0; q < 2; ++q) {
-            SliceJob dj{M[q], SLICE_DIAG, k, T};
-            if ((rc = launch_ozaki_slice(L, g, dj, 1, true, Ds[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_DIAG, k, T}, Ds[0],
+                                      SliceJob{M[1], SLICE_DIAG, k, T}, Ds[1], 1, true))) return rc;
         // E_ik = C_ik - 1/2 L_ik B_kk
         if ((rc = both({OZ_SYGST_FIX, k, T, M[0], Lp, Ds[0], tb, 0.5, 0}, {OZ_SYGST_FIX, k, T, M[1], Lp, Ds[1], tb, 0.5, 0},
                        (long long)m * 2, m * tile_fl, "ozaki_sygst_fix"))) return rc;
-        for (int q = 0; q < 2; ++q) {
-            SliceJob ej{M[q], SLICE_PANEL, k, T};
-            if ((rc = launch_ozaki_slice(L, g, ej, m, true, Xs[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_PANEL, k, T}, Xs[0],
+                                      SliceJob{M[1], SLICE_PANEL, k, T}, Xs[1], m, true))) return rc;
         const long long tasks = (long long)m * (m + 1) / 2;
         // M_ij -= L_ik E_jk^T + E_ik L_jk^T (the two terms of one target in separate launches)
         if ((rc = both({OZ_SYGST_UPD, k, T, M[0], Lp, Xs[0], tb, 1.0, 0}, {OZ_SYGST_UPD, k, T, M[1], Lp, Xs[1], tb, 1.0, 0},
@@ -628,19 +618,15 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
     // B_(m,kk) = W_m (P_(m,kk) - sum_(kk<p<m) L_mp B_(p,kk)), row by row
     for (int m = 1; m < T; ++m) {
         const unsigned char* Wm = Wsl + (size_t)m * tb;
-        for (int q = 0; q < 2; ++q) {
-            SliceJob rj{M[q], SLICE_ROW, m, T};
-            if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_ROW, m, T}, Xs[0],
+                                      SliceJob{M[1], SLICE_ROW, m, T}, Xs[1], m, false))) return rc;
         if ((rc = both({OZ_ROWSOLVE, m, T, M[0], Wm, Xs[0], tb, -1.0, 1}, {OZ_ROWSOLVE, m, T, M[1], Wm, Xs[1], tb, -1.0, 1},
                        (long long)m * 2, m * tile_fl, "ozaki_sygst_solve"))) return rc;
         const int below = T - m - 1;
         if (below == 0) continue;
         const unsigned char* Lp = LS + strict_lower_pos(m + 1, m, T) * tb;
-        for (int q = 0; q < 2; ++q) {
-            SliceJob rj{M[q], SLICE_ROW, m, T};
-            if ((rc = launch_ozaki_slice(L, g, rj, m, false, Xs[q]))) return rc;
-        }
+        if ((rc = launch_ozaki_slice2(L, g, SliceJob{M[0], SLICE_ROW, m, T}, Xs[0],
+                                      SliceJob{M[1], SLICE_ROW, m, T}, Xs[1], m, false))) return rc;
         const long long tasks = (long long)below * m;
         // M_(i,kk) -= L_(i,m) M_(m,kk)
         if ((rc = both({OZ_SYGST_ROWUPD, m, T, M[0], Lp, Xs[0], tb, 1.0, 0}, {OZ_SYGST_ROWUPD, m, T, M[1], Lp, Xs[1], tb, 1.0, 0},
