@@ -373,6 +373,13 @@ static bool same_theta(const double a[3], const double b[3]) {
     return a[0] == b[0] && a[1] == b[1] && a[2] == b[2];
 }
 
+// The inverted diagonal factor tiles, when this context's Cholesky computes them (emulated and
+// mixed paths with the derivative workspace; the inverses of the same factor are bitwise equal
+// wherever they are computed), else nullptr
+static const double* winv_valid(const fbt_ctx* c) {
+    return (c->opts.precision != FBT_PREC_FP64 && c->winv && c->wsl && c->g.nb == 128) ? c->winv : nullptr;
+}
+
 // The launch sequence of one evaluation depends only on these flags (and the context), not on
 // theta, so each variant is captured once as a CUDA graph.
 enum Variant : int { V_LOGLIK = 0, V_LOGLIK_KEEP = 1, V_EVAL = 2, V_EVAL_REUSE = 3, V_EVAL_REUSE_PARTIALS = 4 };
@@ -406,10 +413,10 @@ static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy
     if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl)))
         return cuda_fail((cudaError_t)rc, "potrf");
     EQ(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
-    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv forward");
     if (f.deriv) {
         EQ(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
-        if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
+        if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv backward");
         if ((rc = launch_qform(L, g, c->SA, c->SN, c->vw, c->slots.qform))) return cuda_fail((cudaError_t)rc, "qform");
         // the off-diagonal product slots are indexed by tile; those of diagonal tiles are never
         // written by the transform and must read as zero in the assembly
@@ -543,9 +550,9 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
             return cuda_fail((cudaError_t)rc, "potrf");
     }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
-    if ((rc = launch_trsv(L, g, c->S, c->vy, false))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv forward");
     CK(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
-    if ((rc = launch_trsv(L, g, c->S, c->vw, true))) return cuda_fail((cudaError_t)rc, "trsv backward");
+    if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv backward");
     // Sigma^-1 into SN (W = L^-1 in SA on the way)
     // all digit planes: the plane choice is scaled to Sigma's entries, not to its inverse's
     if ((rc = launch_inverse_from_factor(L, g, c->S, c->SA, c->SN, c->status, c->slices, c->slice_scratch,

@@ -341,8 +341,11 @@ static inline OzGemmJob with_policy(OzGemmJob j, const MixedPolicy& pol) {
 // vector in registers (as the diagonal TRSV does), so one tile's inverse spreads over NB / 8
 // CTAs instead of running column after column in one.  The factor tile is staged in shared memory.
 template <int NB>
-__global__ void __launch_bounds__(256) k_trtri_cols(const double* __restrict__ S, int T, int k,
-                                                   double* __restrict__ W) {
+__global__ void __launch_bounds__(256) k_trtri_cols(const double* __restrict__ S, int T, int k0,
+                                                   double* __restrict__ Wbase) {
+    // tile k = k0 + blockIdx.y, its inverse at Wbase + k nb^2
+    const int k = k0 + (int)blockIdx.y;
+    double* __restrict__ W = Wbase + (long long)k * NB * NB;
     extern __shared__ double A[];
     constexpr int LD = NB + 1;
     constexpr int NBLK = NB / 32;
@@ -406,21 +409,25 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
         L.count();
         if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
         const int m = T - k - 1;
-        if (m == 0) break;
         const bool tensor = NB == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED);
         if (tensor && wtiles && wslices) {
-            // panel on tensor cores: W_k = L_kk^-1 (column-parallel), then L_ik = A_ik W_k^T as an
-            // FP64-accurate tile product (all digit planes), instead of FP64 strip solves
+            // W_k = L_kk^-1 (column-parallel) for every diagonal tile, the last one included: the
+            // panel below uses it, and so do the field's triangular solves
+            const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
+            ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
+            L.begin("trtri_panel");
+            k_trtri_cols<NB><<<dim3(NB / 8, 1), 256, smem_tc, L.stream>>>(S, T, k, wtiles);
+            L.count();
+            if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
+        }
+        if (m == 0) break;
+        if (tensor && wtiles && wslices) {
+            // panel on tensor cores: L_ik = A_ik W_k^T as an FP64-accurate tile product (all digit
+            // planes), instead of FP64 strip solves
             const size_t tb = ozaki_tile_bytes();
             double* Wk = wtiles + (size_t)k * NB * NB;
             unsigned char* Wks = wslices + (size_t)k * tb;
             unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * tb;
-            const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
-            ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
-            L.begin("trtri_panel");
-            k_trtri_cols<NB><<<NB / 8, 256, smem_tc, L.stream>>>(S, T, k, Wk);
-            L.count();
-            if ((rc = L.end(nb3 / 3.0, 16.0 * NB * NB))) return rc;
             SliceJob wj{Wk, SLICE_PTR, 0, T};
             if ((rc = launch_ozaki_slice(L, g, wj, 1, true, Wks))) return rc;
             SliceJob aj{S, SLICE_PANEL, k, T};
@@ -461,43 +468,6 @@ int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, in
     if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
     if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
     return cudaErrorInvalidValue;
-}
-
-// ------------------------------------------------------------------------------------------
-// Inverses of the diagonal factor tiles, W_k = L_kk^-1, all k at once (one CTA each), in place in
-// shared memory by the column-oriented algorithm: from the last column to the first,
-// W_jj = 1 / L_jj and W_(j+1:,j) = -W_jj * W_(j+1:,j+1:) L_(j+1:,j).
-// ------------------------------------------------------------------------------------------
-template <int NB>
-__global__ void __launch_bounds__(256) k_trtri_all(const double* __restrict__ S, int T,
-                                                   double* __restrict__ W) {
-    extern __shared__ double A[];
-    constexpr int LD = NB + 1;
-    __shared__ double t[NB];
-    const int k = blockIdx.x;
-    const double* tile = S + tile_offset(k, k, T, NB);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        A[r + c * LD] = r >= c ? tile[e] : 0.0;
-    }
-    __syncthreads();
-    for (int j = NB - 1; j >= 0; --j) {
-        if (threadIdx.x == 0) A[j + j * LD] = 1.0 / A[j + j * LD];
-        for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) t[i] = A[i + j * LD];
-        __syncthreads();
-        const double ajj = -A[j + j * LD];
-        for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) {
-            double acc = 0.0;
-            for (int q = j + 1; q <= i; ++q) acc = fma(A[i + q * LD], t[q], acc);
-            A[i + j * LD] = acc * ajj;
-        }
-        __syncthreads();
-    }
-    double* out = W + (long long)k * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int r = e % NB, c = e / NB;
-        out[e] = r >= c ? A[r + c * LD] : 0.0;
-    }
 }
 
 // Trace and Frobenius-product partials of the final transformed tiles (one CTA per lower tile,
@@ -562,10 +532,11 @@ static int sygst_ozaki(Launcher& L, const Geom& g, const double* S, double* M0, 
     double* Ys[2] = {Y, Y + NB * NB};
     int rc = 0;
     {
-        const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
-        ensure_smem((const void*)k_trtri_all<NB>, (int)smem);
+        // the same column-parallel kernel as the Cholesky's panels: bitwise the same inverses
+        const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
+        ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
         L.begin("trtri");
-        k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
+        k_trtri_cols<NB><<<dim3(NB / 8, T), 256, smem_tc, L.stream>>>(S, T, 0, Winv);
         L.count();
         if ((rc = L.end(T * nb3 / 3.0, 16.0 * T * NB * NB))) return rc;
         SliceJob wj{Winv, SLICE_PTR, 0, T};
@@ -656,10 +627,10 @@ int launch_inverse_from_factor(Launcher& L, const Geom& g, const double* S, doub
     const double nb3 = (double)NB * NB * NB, tile_fl = 2.0 * nb3;
     unsigned char* Xs = scratch;                                   // up to T sliced tiles
     int rc = 0;
-    const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
-    ensure_smem((const void*)k_trtri_all<NB>, (int)smem);
+    const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
+    ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
     L.begin("trtri");
-    k_trtri_all<NB><<<T, 256, smem, L.stream>>>(S, T, Winv);
+    k_trtri_cols<NB><<<dim3(NB / 8, T), 256, smem_tc, L.stream>>>(S, T, 0, Winv);
     L.count();
     if ((rc = L.end(T * nb3 / 3.0, 16.0 * T * NB * NB))) return rc;
     SliceJob wr{Winv, SLICE_PTR, 0, T};

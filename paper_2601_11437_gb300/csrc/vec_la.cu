@@ -78,6 +78,31 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
         if (s < nblk) vm[lane + 32 * s] = x[s];
 }
 
+// The diagonal step as a product with the inverted diagonal tile W_m = L_mm^-1 (when the
+// emulated path has it): v_m <- W_m v_m (forward) or W_m^T v_m (backward), every row at once.
+// The 256 threads split the columns in 256 / nb parts whose partial sums are added in order.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_trsv_diag_inv(const double* __restrict__ Winv, int nb, int m,
+                                                       double* __restrict__ v) {
+    __shared__ double sv[128];
+    __shared__ double part[4][128];
+    const double* __restrict__ W = Winv + (long long)m * nb * nb;
+    double* vm = v + (long long)m * nb;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
+    __syncthreads();
+    const int parts = blockDim.x / nb, r = threadIdx.x % nb, h = threadIdx.x / nb, cw = nb / parts;
+    double acc = 0.0;
+    for (int c = h * cw; c < (h + 1) * cw; ++c)
+        acc = fma(TRANS ? W[c + (long long)r * nb] : W[r + (long long)c * nb], sv[c], acc);
+    part[h][r] = acc;
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        double y = part[0][r];
+        for (int q = 1; q < parts; ++q) y += part[q][r];
+        vm[r] = y;
+    }
+}
+
 // forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i)
 // backward: v_p -= L(m, p)^T v_m for p < m (one CTA per tile p)
 // Each of the 8 warps takes nb / 8 columns of the tile, so every thread has nb / 8 independent
@@ -122,7 +147,7 @@ __global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ 
     }
 }
 
-int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans) {
+int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans, const double* winv) {
     const int T = g.T, nb = g.nb;
     const size_t smem_upd = (size_t)nb * 9 * sizeof(double);
     const size_t smem_diag = (size_t)nb * (nb + 2) * sizeof(double);
@@ -133,7 +158,8 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
     L.begin(trans ? "trsv_backward" : "trsv_forward");
     if (!trans) {
         for (int m = 0; m < T; ++m) {
-            k_trsv_diag<false><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
+            if (winv) k_trsv_diag_inv<false><<<1, 256, 0, L.stream>>>(winv, nb, m, v);
+            else k_trsv_diag<false><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m + 1 < T) {
                 k_trsv_update<false><<<T - m - 1, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
@@ -142,7 +168,8 @@ int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool tra
         }
     } else {
         for (int m = T - 1; m >= 0; --m) {
-            k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
+            if (winv) k_trsv_diag_inv<true><<<1, 256, 0, L.stream>>>(winv, nb, m, v);
+            else k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             L.count();
             if (m > 0) {
                 k_trsv_update<true><<<m, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
