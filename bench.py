@@ -43,9 +43,9 @@ PRECISIONS = {"fp64": 0, "fp64_emulated": 1}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
-# 992-task launch at n = 4096 (profiles/k_ozaki_gemm_n4096_full.md: 79.4 MB read + 8.8 MB
+# 1984-task launch at n = 4096 (profiles/k_ozaki_gemm_n4096_full.md: 153.8 MB read + 70.9 MB
 # written); the C tiles, which dominate it, grow in proportion to the tasks
-OZAKI_DRAM_BYTES_PER_TASK = (79.404032e6 + 8.782848e6) / 992
+OZAKI_DRAM_BYTES_PER_TASK = (153.799936e6 + 70.884864e6) / 1984
 OZAKI_TASK_FLOPS = 2.0 * 128 * 64 * 128
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
@@ -257,7 +257,7 @@ def run_native(args):
         roof = {"bound": "tensor", "kernel": f"k_ozaki_gemm ({dom})", "achieved": achieved, "peak": bf16_peak,
                 "unit": "TFLOP/s", "frac": achieved / bf16_peak,
                 "traffic": OZAKI_DRAM_BYTES_PER_TASK * tasks_per_launch,
-                "traffic_source": "ncu dram__bytes_read+write of a 992-task launch at n = 4096, "
+                "traffic_source": "ncu dram__bytes_read+write of a 1984-task launch at n = 4096, "
                                   f"scaled to this family's {tasks_per_launch:.0f} tasks per launch",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
                                 else "fallback 1.7 PFLOP/s sustained") + " (of measured)",
