@@ -243,6 +243,7 @@ def run_native(args):
     # dominant kernel: the tile-update family (FP64 DFMA or emulated-FP64 tensor core) with the
     # most device time; the library reports FP64-equivalent flops for both
     gem = {k: v for k, v in prof.items() if k.startswith("gemm") or (k.startswith("ozaki") and k != "ozaki_slice")}
+    w_T = (w.n + args.nb - 1) // args.nb
     dom = max(gem, key=lambda k: gem[k]["ms"])
     per_launch_flops = gem[dom]["flops"] / gem[dom]["launches"]
     per_launch_ms = gem[dom]["ms"] / gem[dom]["launches"]
@@ -267,9 +268,15 @@ def run_native(args):
         roof = {"bound": "alu", "kernel": f"k_gemm_tile ({dom})", "achieved": fp64eq, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": fp64eq / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 DFMA pipe)"}
-    chol = {k: prof[k] for k in ("potrf_diag", "trsm_panel", "trtri_panel", "ozaki_potrf_panel",
-                                 "gemm_potrf_update", "ozaki_potrf_update", "ozaki_slice") if k in prof}
-    chol_tf = sum(v["flops"] for v in chol.values()) / (sum(v["ms"] for v in chol.values()) * 1e-3) / 1e12
+    # Cholesky rate: n^3 / 3 per factorisation over the device time of its critical path (on the
+    # emulated path the diagonal tiles are factored on a side stream, overlapped with the updates)
+    if args.precision == "fp64":
+        chol_fams = ("potrf_diag", "trsm_panel", "gemm_potrf_update")
+    else:
+        chol_fams = ("ozaki_potrf_panel", "ozaki_potrf_update", "cholesky_slice")
+    chol_ms = sum(prof[k]["ms"] for k in chol_fams if k in prof)
+    n_chol = prof["potrf_diag"]["launches"] / w_T if "potrf_diag" in prof else 0
+    chol_tf = n_chol * (w.n ** 3 / 3) / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else None
     total_ms = sum(v["ms"] for v in prof.values())
 
     # end to end: every step re-creates the context from pinned host buffers (locations and
@@ -329,6 +336,8 @@ def run_native(args):
         "cholesky_tflops_fp64_equivalent": chol_tf, "tile_update_tflops_fp64_equivalent": all_gemm_tf,
         "fp64_peak_tflops": FP64_PEAK_TFLOPS,
         "kernel_share": {k: round(v["ms"] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "kernel_share_note": "shares of the summed family times; potrf_diag and trtri_panel run on a side stream, "
+                             "mostly overlapped with the Cholesky's trailing updates",
         "gpu_launches": launches,
         "clocks": ck,
         "e2e": e2e,

@@ -152,6 +152,8 @@ struct fbt_ctx {
     double* pin_theta = nullptr;               // pinned host: sigma^2, alpha, nu, jitter
     EvalOut* pin_out = nullptr;                // pinned host: the result record
     bool graphs = true;
+    cudaStream_t side_stream = nullptr;       // the Cholesky's lookahead (emulated path)
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;        // private stream for captures (the caller's may be
                                               // the legacy default stream, which cannot capture)
     cudaGraphExec_t gexec[5] = {};
@@ -321,6 +323,15 @@ fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device, con
         c->pin_theta = (double*)pin;
         c->pin_out = (EvalOut*)(c->pin_theta + 4);
     }
+    if (c->winv && c->wsl) {
+        if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->side_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            fbt_destroy(c);
+            return FBT_ERR_CUDA;
+        }
+    }
     // staging inside the (not yet used) Sigma slab: sort keys, raw locations, raw field
     long long npow2 = 1;
     while (npow2 < n) npow2 <<= 1;
@@ -410,7 +421,7 @@ static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy
         (rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, f.reuse ? nullptr : c->S, c->SA, c->SN, f.gen_partials,
                               c->status)))
         return cuda_fail((cudaError_t)rc, "generate");
-    if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl)))
+    if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl, c->side_stream, c->side_ev)))
         return cuda_fail((cudaError_t)rc, "potrf");
     EQ(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
     if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv forward");
@@ -546,7 +557,7 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
     } else {
         if ((rc = launch_generate(L, g, c->X, c->Y, c->tc, c->qt, c->S, nullptr, nullptr, false, c->status)))
             return cuda_fail((cudaError_t)rc, "generate");
-        if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl)))
+        if ((rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl, c->side_stream, c->side_ev)))
             return cuda_fail((cudaError_t)rc, "potrf");
     }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
@@ -735,6 +746,9 @@ void fbt_destroy(fbt_ctx* c) {
     for (cudaGraphExec_t& x : c->gexec)
         if (x) cudaGraphExecDestroy(x);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    for (cudaEvent_t& e : c->side_ev)
+        if (e) cudaEventDestroy(e);
     if (c->pin_theta) cudaFreeHost(c->pin_theta);
     delete c->prof;
     if (c->own_ws && c->ws) cudaFree(c->ws);

@@ -108,7 +108,7 @@ struct SliceJob {
 
 // One task of an update launch: 128 rows x 64 columns of one target tile (two per tile).
 enum : int { OZ_POTRF_UPD = 0, OZ_SYGST_UPD = 1, OZ_SYGST_FIX = 2, OZ_SYGST_ROWUPD = 3, OZ_SINGLE = 4,
-             OZ_ROWSOLVE = 5, OZ_LAUUM = 6 };
+             OZ_ROWSOLVE = 5, OZ_LAUUM = 6, OZ_POTRF_COL = 7, OZ_POTRF_REST = 8 };
 struct OzGemmJob {
     int mode, k, T;
     double* C;                     // target slab
@@ -124,12 +124,18 @@ struct OzGemmJob {
         const long long tsk = bid >> 1;
         c0 = (int)(bid & 1) * 64;
         m = mult;
-        if (mode == OZ_POTRF_UPD || mode == OZ_SYGST_UPD) {
+        if (mode == OZ_POTRF_UPD || mode == OZ_SYGST_UPD || mode == OZ_POTRF_REST) {
+            // OZ_POTRF_REST: the trailing update without its first column (jj >= 1)
             int ii, jj;
             tri_decode(tsk, ii, jj);
+            if (mode == OZ_POTRF_REST) { ++ii; ++jj; }
             Ct = C + tile_offset(k + 1 + ii, k + 1 + jj, T, 128);
             sa = slA + (size_t)ii * tile_bytes;
             sb = slB + (size_t)jj * tile_bytes;
+        } else if (mode == OZ_POTRF_COL) {      // the trailing update's first column: (k+1+ii, k+1)
+            Ct = C + tile_offset(k + 1 + (int)tsk, k + 1, T, 128);
+            sa = slA + (size_t)tsk * tile_bytes;
+            sb = slB;
         } else if (mode == OZ_SYGST_FIX) {
             Ct = C + tile_offset(k + 1 + (int)tsk, k, T, 128);
             sa = slA + (size_t)tsk * tile_bytes;
@@ -202,7 +208,8 @@ int launch_generate(Launcher& L, const Geom& g, const double* X, const double* Y
                     double* SN, bool deriv, int* status);
 
 int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntiles, bool rows,
-                       unsigned char* dst);
+                       unsigned char* dst,
+                       const char* family = "ozaki_slice");
 // the same tiles of two jobs (ntiles each) in one launch
 int launch_ozaki_slice2(Launcher& L, const Geom& g, const SliceJob& job0, unsigned char* dst0,
                         const SliceJob& job1, unsigned char* dst1, int ntiles, bool rows);
@@ -210,15 +217,19 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
                       const char* family);
 // up to 4 jobs (tasks[j] tasks each, targets that do not overlap) in one persistent launch
 int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* tasks, int njobs, double flops,
-                            int* status, const char* family);
+                            int* status, const char* family, int reserve_sms = 0);
 
 // tiled Cholesky of the S slab in place (lower tiles), log-det partials per diagonal tile;
 // precision PREC_FP64_OZAKI runs the trailing updates on tensor cores (needs `slices`), and with
 // `wtiles` / `wslices` (T FP64 tiles, T sliced tiles of scratch) the panel solves as well
+// side / ev[2] (optional, tensor path): a second stream and two events for the lookahead, in
+// which the next diagonal tile is factored on one SM while the rest of the trailing update runs
+// on the others
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
                  int precision = PREC_FP64, unsigned char* slices = nullptr,
                  const MixedPolicy& pol = MixedPolicy(), double* wtiles = nullptr,
-                 unsigned char* wslices = nullptr);
+                 unsigned char* wslices = nullptr, cudaStream_t side = nullptr,
+                 cudaEvent_t* ev = nullptr);
 // two-sided transform B = L^-1 M L^-T of both derivative slabs in place, with the trace and
 // Frobenius-product partials of the result
 // precision PREC_FP64_OZAKI: L_slices holds the digit planes of every strictly-lower tile of L

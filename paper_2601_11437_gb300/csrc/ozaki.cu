@@ -430,9 +430,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
 }
 
 int launch_ozaki_slice(Launcher& L, const Geom& g, const SliceJob& job, int ntiles, bool rows,
-                       unsigned char* dst) {
+                       unsigned char* dst, const char* family) {
     if (ntiles <= 0) return 0;
-    L.begin("ozaki_slice");
+    L.begin(family);
     if (rows) k_ozaki_slice<true><<<ntiles * 4, 256, 0, L.stream>>>(g.nb, job, dst, job, dst, ntiles);
     else k_ozaki_slice<false><<<ntiles * 4, 256, 0, L.stream>>>(g.nb, job, dst, job, dst, ntiles);
     L.count();
@@ -455,7 +455,7 @@ int launch_ozaki_gemm(Launcher& L, const OzGemmJob& job, long long ctas, double 
 }
 
 int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* tasks, int njobs, double flops,
-                            int* status, const char* family) {
+                            int* status, const char* family, int reserve_sms) {
     if (njobs < 1 || njobs > 4) return cudaErrorInvalidValue;
     OzJobList jl{};
     long long ctas = 0;
@@ -473,7 +473,9 @@ int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* 
         return v > 0 ? v : 152;
     }();
     ensure_smem((const void*)k_ozaki_gemm, OZ_SMEM);
-    const long long grid = ctas < (long long)sms ? ctas : (long long)sms;    // persistent: one CTA per SM
+    // persistent: one CTA per SM, reserve_sms of them left to concurrent work
+    const long long avail = (long long)sms - reserve_sms > 1 ? (long long)sms - reserve_sms : 1;
+    const long long grid = ctas < avail ? ctas : avail;
     L.begin(family);
     k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
     L.count();

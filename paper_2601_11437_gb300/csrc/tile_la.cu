@@ -390,6 +390,73 @@ __global__ void __launch_bounds__(256) k_trtri_cols(const double* __restrict__ S
     }
 }
 
+// Tensor-core Cholesky with lookahead.  Per step k: the panel L_ik = A_ik W_k^T (tensor cores),
+// its digit planes, the first column of the trailing update, then the rest of the update as a
+// persistent launch on all SMs but one while the side stream factors and inverts diagonal tile
+// k + 1 on the free SM (its inputs are final once the first column is updated).
+template <int NB>
+static int potrf_tensor(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
+                        unsigned char* slices, const MixedPolicy& pol, double* wtiles, unsigned char* wslices,
+                        cudaStream_t side, cudaEvent_t* ev) {
+    const int T = g.T;
+    const size_t tb = ozaki_tile_bytes();
+    const double nb3 = (double)NB * NB * NB, nb2 = (double)NB * NB;
+    const size_t smem_potrf = (size_t)NB * (NB + 1) * sizeof(double);
+    const size_t smem_tc = (size_t)NB * (NB + 2) * sizeof(double);
+    ensure_smem((const void*)k_potrf_diag<NB>, (int)smem_potrf);
+    ensure_smem((const void*)k_trtri_cols<NB>, (int)smem_tc);
+    Launcher LS = L;
+    LS.stream = side;
+    auto diag = [&](Launcher& X, int k) -> int {
+        X.begin("potrf_diag");
+        k_potrf_diag<NB><<<1, 512, smem_potrf, X.stream>>>(S, T, k, logdet_slots, status);
+        X.count();
+        int r = X.end(nb3 / 3.0, 16.0 * nb2);
+        if (r) return r;
+        X.begin("trtri_panel");
+        k_trtri_cols<NB><<<dim3(NB / 8, 1), 256, smem_tc, X.stream>>>(S, T, k, wtiles);
+        X.count();
+        return X.end(nb3 / 3.0, 16.0 * nb2);
+    };
+    int rc = diag(L, 0);
+    if (rc) return rc;
+    for (int k = 0; k + 1 < T; ++k) {
+        const int m = T - k - 1;
+        unsigned char* Wks = wslices + (size_t)k * tb;
+        unsigned char* panel = slices + strict_lower_pos(k + 1, k, T) * tb;
+        SliceJob wj{wtiles + (size_t)k * NB * NB, SLICE_PTR, 0, T};
+        if ((rc = launch_ozaki_slice(L, g, wj, 1, true, Wks, "cholesky_slice"))) return rc;
+        SliceJob aj{S, SLICE_PANEL, k, T};
+        if ((rc = launch_ozaki_slice(L, g, aj, m, true, panel, "cholesky_slice"))) return rc;   // digits of A_ik
+        OzGemmJob pj{OZ_SYGST_FIX, k, T, S, panel, Wks, tb, -1.0, 1};
+        if ((rc = launch_ozaki_gemm(L, pj, (long long)m * 2, m * 2.0 * nb3, status, "ozaki_potrf_panel"))) return rc;
+        // digit planes of panel k, kept for the two-sided transforms
+        if ((rc = launch_ozaki_slice(L, g, aj, m, true, panel, "cholesky_slice"))) return rc;
+        OzGemmJob cj = with_policy({OZ_POTRF_COL, k, T, S, panel, panel, tb, 1.0, 0}, pol);
+        const double fl_col = (m - 1) * 2.0 * nb3 + nb3 + nb2;
+        if ((rc = launch_ozaki_gemm(L, cj, (long long)m * 2, fl_col, status, "ozaki_potrf_update"))) return rc;
+        if (m == 1) {
+            if ((rc = diag(L, k + 1))) return rc;
+            continue;
+        }
+        OzGemmJob rj = with_policy({OZ_POTRF_REST, k, T, S, panel, panel, tb, 1.0, 0}, pol);
+        const long long rest = (long long)(m - 1) * m;      // (m - 1) m / 2 tiles, two tasks each
+        const double fl_rest = (double)(m - 1) * (m - 2) / 2 * 2.0 * nb3 + (m - 1) * (nb3 + nb2);
+        if (side) {
+            if (cudaEventRecord(ev[0], L.stream) != cudaSuccess || cudaStreamWaitEvent(side, ev[0], 0) != cudaSuccess)
+                return cudaGetLastError();
+            if ((rc = diag(LS, k + 1))) return rc;
+            if (cudaEventRecord(ev[1], side) != cudaSuccess) return cudaGetLastError();
+            if ((rc = launch_ozaki_gemm_multi(L, &rj, &rest, 1, fl_rest, status, "ozaki_potrf_update", 1))) return rc;
+            if (cudaStreamWaitEvent(L.stream, ev[1], 0) != cudaSuccess) return cudaGetLastError();
+        } else {
+            if ((rc = launch_ozaki_gemm_multi(L, &rj, &rest, 1, fl_rest, status, "ozaki_potrf_update"))) return rc;
+            if ((rc = diag(L, k + 1))) return rc;
+        }
+    }
+    return rc;
+}
+
 template <int NB>
 static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
                       int precision, unsigned char* slices, const MixedPolicy& pol, double* wtiles,
@@ -464,7 +531,9 @@ static int potrf_impl(Launcher& L, const Geom& g, double* S, double* logdet_slot
 
 int launch_potrf(Launcher& L, const Geom& g, double* S, double* logdet_slots, int* status,
                  int precision, unsigned char* slices, const MixedPolicy& pol, double* wtiles,
-                 unsigned char* wslices) {
+                 unsigned char* wslices, cudaStream_t side, cudaEvent_t* ev) {
+    if (g.nb == 128 && (precision == PREC_FP64_OZAKI || precision == PREC_MIXED) && wtiles && wslices && slices)
+        return potrf_tensor<128>(L, g, S, logdet_slots, status, slices, pol, wtiles, wslices, side, side ? ev : nullptr);
     if (g.nb == 128) return potrf_impl<128>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
     if (g.nb == 64) return potrf_impl<64>(L, g, S, logdet_slots, status, precision, slices, pol, wtiles, wslices);
     return cudaErrorInvalidValue;
