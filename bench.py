@@ -368,9 +368,13 @@ def run_batch(args):
     driven concurrently (host thread pool, one stream per thread), each from its theta^(0) state."""
     import torch
     import paper_2601_11437_gb300 as fbt
+    from paper_2601_11437_gb300 import sharding
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
-    batch = load_batch(args.workload)
+    full = load_batch(args.workload)
+    # N > 1: the fields are independent units, shared out by cost; no exchange until the end
+    mine = sharding.partition([f.n ** 3 for f, _, _ in full], world)[rank]
+    batch = [full[i] for i in mine]
     prec = PRECISIONS[args.precision]
     ctxs = [fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=prec) for _, locs, z in batch]
     theta0s = np.array([f.theta0 for f, _, _ in batch])
@@ -391,6 +395,7 @@ def run_batch(args):
     for c in run_ctxs:
         fbt.fbt_launch_count(c, reset=True)
     clocks = Clocks(local)
+    barrier(world, local)
     torch.cuda.synchronize()
     clocks.start()
     t0 = time.perf_counter()
@@ -403,18 +408,36 @@ def run_batch(args):
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     ck = clocks.stop()
+    barrier(world, local)
+    sec = max_over_ranks(world, sec, local)
     launches = sum(fbt.fbt_launch_count(c) for c in run_ctxs)
     for c in ctxs:
         fbt.fbt_destroy(c)
+    n_stepped = len(running)
+    if world > 1:
+        # the one exchange: every field's 13-double record of its last step, gathered in field order
+        import torch.distributed as dist
+        g = dist.new_group(backend="gloo")
+        pos = {q: i for i, q in enumerate(running)}
+        recs = []
+        for q in range(len(batch)):                 # fields that did not step report their start
+            s_ = st[pos[q]] if q in pos else st0[q]
+            recs.append([s_.loglik, *s_.score[:], *s_.fisher[:]])
+        sharding.gather_records(mine, recs, len(full), group=g)
+        tot = torch.tensor([float(n_stepped), flops, float(launches)], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tot)
+        n_stepped, flops, launches = int(tot[0].item()), float(tot[1].item()), int(tot[2].item())
     if rank != 0:
         return 0
     line = {
-        "metric": "fields x Fisher-BT iterations/s (batched fields)", "value": len(running) * args.steps / sec,
+        "metric": "fields x Fisher-BT iterations/s (batched fields)", "value": n_stepped * args.steps / sec,
         "unit": "field-iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "fields": len(batch), "fields_stepped": len(running),
-                   "n_range": [int(ns.min()), int(ns.max())], "sum_n3": float((ns ** 3).sum()),
+        "config": {"workload": args.workload, "fields": len(full), "fields_stepped": n_stepped,
+                   "parallelism": f"fields sharded over {world} rank(s) by n^3, records gathered",
+                   "n_range": [min(f.n for f, _, _ in full), max(f.n for f, _, _ in full)],
+                   "sum_n3": float(sum(float(f.n) ** 3 for f, _, _ in full)),
                    "precision": args.precision, "threads": args.threads, "nb": args.nb,
                    "timing": "host wall clock around each batched call (it synchronises every stream)"},
         "aggregate_tflops_fp64_equivalent": flops / sec / 1e12,
