@@ -50,6 +50,26 @@ def test_generation_matches_oracle(n, nb, theta):
     fbt.fbt_destroy(ctx)
 
 
+@pytest.mark.parametrize("theta", [(0.05, 0.05, 0.05), (0.1, 0.1, 0.1), (1.5, 1.55, 1.3), (2.0, 0.8, 1.0),
+                                   (1.0, 0.02, 2.5), (1.0, 0.3, 4.0), (1.0, 0.015, 0.6)],
+                         ids=["nu0.05", "nu0.1", "alpha1.55", "alpha0.8", "nu2.5", "nu4", "alpha0.015"])
+def test_generation_matches_oracle_at_extreme_parameters(theta):
+    # the simulation study's settings and beyond: tiny nu (slowly decaying quadrature terms),
+    # ranges far above the domain (every x below 1, many nodes) and far below it (x up to 90,
+    # the finer levels), large nu
+    import paper_2601_11437_gb300 as fbt
+    n = 257
+    locs, z = inputs.uniform_locations(n, 12), inputs.standard_normal(n, 12)
+    ctx = fbt.fbt_create(locs, z, nb=128)
+    fbt.fbt_generate(ctx, theta, True)
+    perm = fbt.fbt_copy_perm(ctx)
+    ref = matern.covariance(locs[perm], theta)
+    for which, key in ((0, "S"), (1, "S_alpha"), (2, "S_nu")):
+        got = dense_from_ctx(fbt, ctx, which)
+        assert rel_err(got, ref[key]) < TOL_ENTRY, (which, rel_err(got, ref[key]))
+    fbt.fbt_destroy(ctx)
+
+
 def test_padding_is_identity():
     import paper_2601_11437_gb300 as fbt
     n, nb = 70, 64
