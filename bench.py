@@ -39,7 +39,7 @@ from paper_2601_11437_gb300 import inputs  # noqa: E402
 
 FIELDS = os.path.join(ROOT, "tests", "golden", "fields")
 METRIC = "Fisher-BT iterations/s (FP64 path)"
-PRECISIONS = {"fp64": 0, "fp64_emulated": 1}
+PRECISIONS = {"fp64": 0, "fp64_emulated": 1, "mixed": 2}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
@@ -328,7 +328,10 @@ def run_native(args):
                    "arithmetic": {"fp64": "FP64 DFMA tile updates",
                                   "fp64_emulated": "FP64-accurate tile updates from exact BF16 digit products "
                                                    "on tcgen05 tensor cores (7 x 8-bit balanced slices, FP32 TMEM groups, "
-                                                   "FP64 recombination); all else FP64"}[args.precision],
+                                                   "FP64 recombination); all else FP64",
+                                  "mixed": "tile updates from 7, 3 or 1 BF16 digit planes per tile product, chosen "
+                                           "from a bound on the product's entries; diagonal tiles and all else FP64"
+                                  }[args.precision],
                    "theta0": w.theta0, "jitter": w.jitter, "parallelism": f"replicas{world}",
                    "evaluations_per_step": evals / args.steps,
                    "l2": "no flush: each step streams 3 x 1.1 GB of tile slabs, far above the 129 MB L2"},

@@ -131,6 +131,7 @@ struct fbt_ctx {
     unsigned char* wsl = nullptr;            // their digit planes
     unsigned char* wcs = nullptr;            // their digit planes, column-sliced
     double* yscratch = nullptr;              // two scratch tiles
+    double* vx = nullptr;                    // one solved block of a triangular solve
     Profiler* prof = nullptr;
     long long launches = 0;
     long long h2d_bytes = 0, d2h_bytes = 0;
@@ -220,6 +221,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pws = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // digit planes of W_k
     char* pwc = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // W_k, column-sliced
     char* pyy = ed ? take((size_t)2 * nb * nb * sizeof(double)) : nullptr;       // two scratch tiles
+    char* pvx = ed ? take((size_t)nb * sizeof(double)) : nullptr;                // one solved block
     if (base && c) {
         c->slices = (unsigned char*)psl;
         c->slice_scratch = (unsigned char*)psx;
@@ -227,6 +229,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
         c->wsl = (unsigned char*)pws;
         c->wcs = (unsigned char*)pwc;
         c->yscratch = (double*)pyy;
+        c->vx = (double*)pvx;
         c->X = (double*)pX; c->Y = (double*)pY; c->Z = (double*)pZ;
         c->vy = (double*)pvy; c->vw = (double*)pvw;
         c->perm = (long long*)pperm; c->bbox = (double*)pbbox;
@@ -424,10 +427,10 @@ static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy
     if (!f.reuse && (rc = launch_potrf(L, g, c->S, c->slots.logdet, c->status, c->opts.precision, c->slices, pol, c->winv, c->wsl, c->side_stream, c->side_ev)))
         return cuda_fail((cudaError_t)rc, "potrf");
     EQ(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
-    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c), c->vx))) return cuda_fail((cudaError_t)rc, "trsv forward");
     if (f.deriv) {
         EQ(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
-        if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv backward");
+        if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c), c->vx))) return cuda_fail((cudaError_t)rc, "trsv backward");
         if ((rc = launch_qform(L, g, c->SA, c->SN, c->vw, c->slots.qform))) return cuda_fail((cudaError_t)rc, "qform");
         // the off-diagonal product slots are indexed by tile; those of diagonal tiles are never
         // written by the transform and must read as zero in the assembly
@@ -561,9 +564,9 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
             return cuda_fail((cudaError_t)rc, "potrf");
     }
     CK(cudaMemcpyAsync(c->vy, c->Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy z");
-    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv forward");
+    if ((rc = launch_trsv(L, g, c->S, c->vy, false, winv_valid(c), c->vx))) return cuda_fail((cudaError_t)rc, "trsv forward");
     CK(cudaMemcpyAsync(c->vw, c->vy, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, c->stream), "copy y");
-    if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c)))) return cuda_fail((cudaError_t)rc, "trsv backward");
+    if ((rc = launch_trsv(L, g, c->S, c->vw, true, winv_valid(c), c->vx))) return cuda_fail((cudaError_t)rc, "trsv backward");
     // Sigma^-1 into SN (W = L^-1 in SA on the way)
     // all digit planes: the plane choice is scaled to Sigma's entries, not to its inverse's
     if ((rc = launch_inverse_from_factor(L, g, c->S, c->SA, c->SN, c->status, c->slices, c->slice_scratch,

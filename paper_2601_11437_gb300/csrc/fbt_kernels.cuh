@@ -257,8 +257,10 @@ int launch_adjoint_reduce(Launcher& L, const Geom& g, const double* Xs, const do
                           const QuadTables* qt, double* slots, int* status);
 
 // v <- L^-1 v (trans = false) or v <- L^-T v (trans = true), tile by tile
-// winv (optional): the inverted diagonal factor tiles; the diagonal steps then multiply by them
-int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans, const double* winv = nullptr);
+// winv (optional): the inverted diagonal factor tiles; the diagonal steps then multiply by them,
+// writing each solved block to vx (nb doubles of scratch, required with winv) first
+int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans, const double* winv = nullptr,
+                double* vx = nullptr);
 // per-tile partials of w^T M0 w and w^T M1 w over the lower tiles (off-diagonal tiles doubled)
 int launch_qform(Launcher& L, const Geom& g, const double* M0, const double* M1, const double* w,
                  double* qform_slots);

@@ -78,103 +78,122 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ S,
         if (s < nblk) vm[lane + 32 * s] = x[s];
 }
 
+// One 32-entry chunk q of A x (TRANS = false) or A^T x (TRANS = true) for a column-major
+// nb x nb tile A and the vector x staged in shared memory; 256 threads, nb in {64, 128}. Each
+// output entry is owned by one CTA and summed in a fixed order, so results are reproducible.
+// The value is returned in threads 0..31 (entry 32 q + threadIdx.x).
+template <bool TRANS>
+__device__ __forceinline__ double chunk_matvec(const double* __restrict__ A, int nb, const double* sx,
+                                               double* part, int q) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (!TRANS) {
+        // rows 32 q + lane; warp w takes columns [w nb / 8, (w + 1) nb / 8): every load of a warp
+        // is 32 consecutive doubles of one column, all nb / 8 of them in flight at once
+        const int cw = nb >> 3, c0 = warp * cw;
+        const double* __restrict__ a = A + 32 * q + lane + (long long)c0 * nb;
+        double acc = 0.0;
+#pragma unroll 16
+        for (int c = 0; c < cw; ++c) acc = fma(a[(long long)c * nb], sx[c0 + c], acc);
+        part[warp * 32 + lane] = acc;
+    } else {
+        // entries 32 q + 4 w + j are dots of whole (contiguous) columns with x, lanes over rows
+        const int nr = nb >> 5;
+        double acc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double* __restrict__ col = A + (long long)(32 * q + 4 * warp + j) * nb;
+            acc[j] = 0.0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (s < nr) acc[j] = fma(col[lane + 32 * s], sx[lane + 32 * s], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+            if (lane == 0) part[4 * warp + j] = acc[j];
+        }
+    }
+    __syncthreads();
+    double y = 0.0;
+    if (threadIdx.x < 32) {
+        if (!TRANS) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) y += part[w * 32 + threadIdx.x];
+        } else {
+            y = part[threadIdx.x];
+        }
+    }
+    return y;
+}
+
 // The diagonal step as a product with the inverted diagonal tile W_m = L_mm^-1 (when the
-// emulated path has it): v_m <- W_m v_m (forward) or W_m^T v_m (backward), every row at once.
-// The 256 threads split the columns in 256 / nb parts whose partial sums are added in order.
+// emulated path has it): x = W_m v_m (forward) or W_m^T v_m (backward), written to x (nb
+// doubles) rather than in place, because the nb / 32 CTAs of the launch all read v_m.
 template <bool TRANS>
 __global__ void __launch_bounds__(256) k_trsv_diag_inv(const double* __restrict__ Winv, int nb, int m,
-                                                       double* __restrict__ v) {
-    __shared__ double sv[128];
-    __shared__ double part[4][128];
-    const double* __restrict__ W = Winv + (long long)m * nb * nb;
-    double* vm = v + (long long)m * nb;
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
-    __syncthreads();
-    const int parts = blockDim.x / nb, r = threadIdx.x % nb, h = threadIdx.x / nb, cw = nb / parts;
-    double acc = 0.0;
-    for (int c = h * cw; c < (h + 1) * cw; ++c)
-        acc = fma(TRANS ? W[c + (long long)r * nb] : W[r + (long long)c * nb], sv[c], acc);
-    part[h][r] = acc;
-    __syncthreads();
-    if (threadIdx.x < nb) {
-        double y = part[0][r];
-        for (int q = 1; q < parts; ++q) y += part[q][r];
-        vm[r] = y;
-    }
-}
-
-// forward: v_i -= L(i, m) v_m for i > m (one CTA per tile i)
-// backward: v_p -= L(m, p)^T v_m for p < m (one CTA per tile p)
-// Each of the 8 warps takes nb / 8 columns of the tile, so every thread has nb / 8 independent
-// loads in flight; the warps' partial sums are added in a fixed order.
-template <bool TRANS>
-__global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ S, int T, int nb,
-                                                     int m, double* __restrict__ v) {
-    extern __shared__ double sv[];            // v_m [nb], then partial sums [8][nb]
-    double* part = sv + nb;
+                                                       const double* __restrict__ v, double* __restrict__ x) {
+    __shared__ double sb[128];
+    __shared__ double part[256];
     const double* vm = v + (long long)m * nb;
-    for (int d = threadIdx.x; d < nb; d += blockDim.x) sv[d] = vm[d];
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) sb[d] = vm[d];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cw = nb / 8, cbeg = warp * cw;
-    if (!TRANS) {
-        const int i = m + 1 + blockIdx.x;
-        const double* __restrict__ A = S + tile_offset(i, m, T, nb);
-        for (int r = lane; r < nb; r += 32) {          // rows r of columns cbeg .. cbeg + cw - 1
-            double acc = 0.0;
-#pragma unroll 8
-            for (int c = cbeg; c < cbeg + cw; ++c) acc = fma(A[r + (long long)c * nb], sv[c], acc);
-            part[warp * nb + r] = acc;
-        }
-        __syncthreads();
-        double* vi = v + (long long)i * nb;
-        for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-            double acc = 0.0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) acc += part[w * nb + r];
-            vi[r] -= acc;
-        }
-    } else {
-        const int pt = blockIdx.x;
-        const double* __restrict__ A = S + tile_offset(m, pt, T, nb);
-        double* vp = v + (long long)pt * nb;
-        for (int c = cbeg; c < cbeg + cw; ++c) {       // column c of L(m, p): a dot with v_m
-            double acc = 0.0;
-            for (int r = lane; r < nb; r += 32) acc = fma(A[r + (long long)c * nb], sv[r], acc);
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-            if (lane == 0) vp[c] -= acc;
-        }
-    }
+    const double y = chunk_matvec<TRANS>(Winv + (long long)m * nb * nb, nb, sb, part, blockIdx.x);
+    if (threadIdx.x < 32) x[32 * blockIdx.x + threadIdx.x] = y;
 }
 
-int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans, const double* winv) {
+// forward: v_i -= L(i, m) x for i > m; backward: v_p -= L(m, p)^T x for p < m, where x is
+// the solved block m. Grid (nb / 32, tiles): CTA (q, t) owns entries 32 q .. 32 q + 31 of one
+// updated block, so a step reads its column (row) of tiles with nb / 32 times as many CTAs as
+// tiles. When copy_x is set, x came from k_trsv_diag_inv and the first tile's CTAs also store
+// it into v_m (nothing else in the launch touches v_m).
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_trsv_update(const double* __restrict__ S, int T, int nb, int m,
+                                                     const double* x, double* v, int copy_x) {
+    __shared__ double sx[128];
+    __shared__ double part[256];
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) sx[d] = x[d];
+    __syncthreads();
+    const int q = blockIdx.x;
+    if (copy_x && blockIdx.y == 0 && threadIdx.x < 32)
+        v[(long long)m * nb + 32 * q + threadIdx.x] = sx[32 * q + threadIdx.x];
+    const int t = TRANS ? (int)blockIdx.y : m + 1 + (int)blockIdx.y;
+    const double* __restrict__ A = S + (TRANS ? tile_offset(m, t, T, nb) : tile_offset(t, m, T, nb));
+    const double y = chunk_matvec<TRANS>(A, nb, sx, part, q);
+    if (threadIdx.x < 32) v[(long long)t * nb + 32 * q + threadIdx.x] -= y;
+}
+
+int launch_trsv(Launcher& L, const Geom& g, const double* S, double* v, bool trans, const double* winv,
+                double* vx) {
     const int T = g.T, nb = g.nb;
-    const size_t smem_upd = (size_t)nb * 9 * sizeof(double);
+    if (winv && !vx) return (int)cudaErrorInvalidValue;
     const size_t smem_diag = (size_t)nb * (nb + 2) * sizeof(double);
     ensure_smem((const void*)k_trsv_diag<false>, (int)smem_diag);
     ensure_smem((const void*)k_trsv_diag<true>, (int)smem_diag);
     const double tb = 8.0 * nb * nb;
+    const int chunks = nb / 32;
     int rc = 0;
     L.begin(trans ? "trsv_backward" : "trsv_forward");
-    if (!trans) {
-        for (int m = 0; m < T; ++m) {
-            if (winv) k_trsv_diag_inv<false><<<1, 256, 0, L.stream>>>(winv, nb, m, v);
+    for (int k = 0; k < T; ++k) {
+        const int m = trans ? T - 1 - k : k;
+        const int rest = trans ? m : T - 1 - m;          // tiles updated by this step
+        if (winv) {
+            if (trans) k_trsv_diag_inv<true><<<chunks, 256, 0, L.stream>>>(winv, nb, m, v, vx);
+            else k_trsv_diag_inv<false><<<chunks, 256, 0, L.stream>>>(winv, nb, m, v, vx);
+        } else {
+            if (trans) k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
             else k_trsv_diag<false><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
-            L.count();
-            if (m + 1 < T) {
-                k_trsv_update<false><<<T - m - 1, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
-                L.count();
-            }
         }
-    } else {
-        for (int m = T - 1; m >= 0; --m) {
-            if (winv) k_trsv_diag_inv<true><<<1, 256, 0, L.stream>>>(winv, nb, m, v);
-            else k_trsv_diag<true><<<1, 256, smem_diag, L.stream>>>(S, T, nb, m, v);
+        L.count();
+        const double* x = winv ? vx : v + (long long)m * nb;
+        if (rest > 0) {
+            const dim3 grid(chunks, rest);
+            if (trans) k_trsv_update<true><<<grid, 256, 0, L.stream>>>(S, T, nb, m, x, v, winv ? 1 : 0);
+            else k_trsv_update<false><<<grid, 256, 0, L.stream>>>(S, T, nb, m, x, v, winv ? 1 : 0);
             L.count();
-            if (m > 0) {
-                k_trsv_update<true><<<m, 256, smem_upd, L.stream>>>(S, T, nb, m, v);
-                L.count();
-            }
+        } else if (winv) {
+            const cudaError_t e = cudaMemcpyAsync(v + (long long)m * nb, vx, (size_t)nb * sizeof(double),
+                                                  cudaMemcpyDeviceToDevice, L.stream);
+            if (e != cudaSuccess) return (int)e;
         }
     }
     // algorithmic: n_pad^2 flops (one multiply-add per stored lower entry), the lower triangle read once

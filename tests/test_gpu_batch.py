@@ -34,7 +34,7 @@ def contexts(batch, precision, nb=128):
     return [fbt.fbt_create(locs, z, nb=nb, precision=precision) for _, locs, z in batch]
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp64_emulated"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "fp64_emulated", "mixed"])
 def test_eval_batch_is_bitwise_the_one_by_one_path(small_batch, precision):
     import paper_2601_11437_gb300 as fbt
     thetas = np.array([[f.theta0, f.theta_true] for f, _, _ in small_batch])       # (F, 2, 3)
