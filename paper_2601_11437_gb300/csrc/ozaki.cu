@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
             const int* __restrict__ exp_a = (const int*)(sa + OZ_TILE_BYTES);
             const int* __restrict__ exp_b = (const int*)(sb + OZ_TILE_BYTES);
-            const int er = exp_a[r] - 46 + ilogb(fabs(mult));     // |mult| is a power of two
+            // |mult| is a power of two: its exponent is read from the bits (ilogb costs a dozen
+            // instructions on the narrow FP64 pipe, per thread and task)
+            const int er = exp_a[r] - 46 + (int)((__double_as_longlong(mult) >> 52) & 0x7FF) - 1023;
             const bool assign = job.assign != 0;
             const bool negm = mult < 0.0;
             double* __restrict__ Cr = C + r + (long long)(c0 + chalf) * 128;
