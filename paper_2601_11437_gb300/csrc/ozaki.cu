@@ -242,6 +242,9 @@ struct OzJobList {
     }
 };
 
+// MIXED: the job list may use fewer digit planes per task (compiled separately, so that the
+// FP64-accurate path carries no plane-count logic)
+template <bool MIXED>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, long long ntasks, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
     unsigned char* stA = oz_smem;                                    // [4][32 KB]
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 long long lt;
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, C, c0, mult);
-                const int np = task_planes(job, sa, sb);
+                const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
                     if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1))) {
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 long long lt;
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, Cq, cq, mq);
-                const int np = task_planes(job, sa, sb);
+                const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
                 if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1))) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool bad = false;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             long long lt;
             const OzGemmJob& job = jobs.pick(t, lt);
             job.task(lt, sa, sb, C, c0, mult);
-            const int np = task_planes(job, sa, sb);
+            const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
             if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             long long fx[OZ_EPI_COLS];
@@ -386,11 +389,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                     const int iv2 = __float2int_rn(__uint_as_float(v[2][j]));
                     const int iv3 = __float2int_rn(__uint_as_float(v[3][j]));
                     const int iv4 = __float2int_rn(__uint_as_float(v[4][j]));
-                    const int iv5 = (__float_as_int(__uint_as_float(v[5][j]) + 50331648.0f) - 0x4C400000) * 4;
-                    const int iv6 = (__float_as_int(__uint_as_float(v[6][j]) + 50331648.0f) - 0x4C400000) * 4;
+                    const float t56 = fmaf(__uint_as_float(v[6][j]), 0.00390625f, __uint_as_float(v[5][j]));
+                    const int r56 = __float_as_int(fmaf(t56, 0.00390625f, 12582912.0f)) - 0x4B400000;
                     const int p01 = iv0 * 256 + iv1, p23 = iv2 * 256 + iv3;
-                    const long long low = (long long)iv5 * 256 + iv6 + (1ll << 15);
-                    fx[cb + j] = (long long)p01 * (1ll << 24) + (long long)p23 * (1ll << 8) + iv4 + (low >> 16);
+                    fx[cb + j] = (long long)p01 * (1ll << 24) + (long long)p23 * (1ll << 8) + (iv4 + r56);
                 }
             }
             // accumulators are in registers: hand TMEM back to the MMA warp
@@ -405,18 +407,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             const bool assign = job.assign != 0;
             const bool negm = mult < 0.0;
             double* __restrict__ Cr = C + r + (long long)(c0 + chalf) * 128;
-            // C values are loaded 16 at a time before any is stored, so their latencies overlap
+            // C values are loaded 8 at a time before any is stored, so their latencies overlap
 #pragma unroll
-            for (int h = 0; h < OZ_EPI_COLS; h += 16) {
-                double cv[16];
-                int eb[16];
+            for (int h = 0; h < OZ_EPI_COLS; h += 8) {
+                double cv[8];
+                int eb[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     cv[j] = assign ? 0.0 : Cr[(long long)(h + j) * 128];
                     eb[j] = exp_b[c0 + chalf + h + j];
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     const double y = fx_to_double(negm ? -fx[h + j] : fx[h + j], er + eb[j]);
                     Cr[(long long)(h + j) * 128] = cv[j] - y;
                 }
@@ -474,12 +476,16 @@ int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* 
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         return v > 0 ? v : 152;
     }();
-    ensure_smem((const void*)k_ozaki_gemm, OZ_SMEM);
+    bool mixed = false;
+    for (int j = 0; j < njobs; ++j) mixed = mixed || job[j].mixed != 0;
+    ensure_smem((const void*)k_ozaki_gemm<false>, OZ_SMEM);
+    ensure_smem((const void*)k_ozaki_gemm<true>, OZ_SMEM);
     // persistent: one CTA per SM, reserve_sms of them left to concurrent work
     const long long avail = (long long)sms - reserve_sms > 1 ? (long long)sms - reserve_sms : 1;
     const long long grid = ctas < avail ? ctas : avail;
     L.begin(family);
-    k_ozaki_gemm<<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
+    if (mixed) k_ozaki_gemm<true><<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
+    else k_ozaki_gemm<false><<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
     L.count();
     return L.end(flops, 0.0);
 }
