@@ -43,9 +43,9 @@ PRECISIONS = {"fp64": 0, "fp64_emulated": 1, "mixed": 2}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
-# 1984-task launch at n = 4096 (profiles/k_ozaki_gemm_n4096_full.md: 153.9 MB read + 71.1 MB
+# 1984-task launch at n = 4096 (profiles/k_ozaki_gemm_n4096_full.md: 153.3 MB read + 70.8 MB
 # written); the C tiles, which dominate it, grow in proportion to the tasks
-OZAKI_DRAM_BYTES_PER_TASK = (153.851904e6 + 71.148032e6) / 1984
+OZAKI_DRAM_BYTES_PER_TASK = (153.323776e6 + 70.84672e6) / 1984
 OZAKI_TASK_FLOPS = 2.0 * 128 * 64 * 128
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
