@@ -43,7 +43,7 @@ constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier
 
 size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }   // digits + row exponents
 
-// byte offset of digit (row, k) of plane p inside a sliced tile: K chunk k/16 (all 8 planes of a
+// byte offset of digit (row, k) of plane p inside a sliced tile: K chunk k/16 (all 7 planes of a
 // chunk are contiguous, so one bulk copy fetches an A stage), plane p, then the canonical K-major
 // core-matrix layout of a 128 x 16 block (LBO = 128 B, SBO = 256 B)
 __host__ __device__ inline uint32_t oz_off(int p, int row, int k) {
@@ -187,7 +187,7 @@ __device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
 }
 
 // ------------------------------------------------------------------------------------------
-// the update kernel: one CTA = 128 rows x 32 columns of one target tile, 8 warps
+// the tile-update kernel and its epilogue helpers
 // ------------------------------------------------------------------------------------------
 __device__ inline void tmem_ld8x(uint32_t taddr, uint32_t r[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -216,7 +216,7 @@ constexpr int OZ_EPI_WARPS = 16;                        // 4 per TMEM lane quart
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_EPI_COLS = OZ_N * 4 / OZ_EPI_WARPS;   // accumulator columns per epilogue warp
 
-// Digit planes used for a task: 8 (FP64-accurate); in the mixed path 3 or 1 when the operand
+// Digit planes used for a task: 7 (FP64-accurate); in the mixed path 3 or 1 when the operand
 // tiles' largest entries, 2^ea and 2^eb, make the product small against the thresholds.
 __device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa, const unsigned char* sb) {
     if (!job.mixed) return OZ_S;
@@ -247,8 +247,8 @@ struct OzJobList {
 template <bool MIXED>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, long long ntasks, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
-    unsigned char* stA = oz_smem;                                    // [4][32 KB]
-    unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [4][16 KB]
+    unsigned char* stA = oz_smem;                                    // [4][28 KB]
+    unsigned char* stB = oz_smem + OZ_STAGES * OZ_STAGE_A;           // [4][14 KB]
     uint64_t* bars = (uint64_t*)(oz_smem + OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B));
     uint64_t* full = bars;                   // [4] stage loaded
     uint64_t* empty = bars + OZ_STAGES;      // [4] stage consumed by the MMAs
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
 
     if (warp == 1) {
         if (lane == 0) {
-            // producer: stages (task, kc) in order; stage s = it & 1 is reused every other step
+            // producer: stages (task, kc) in order through the ring, stage s = it % OZ_STAGES
             long long it = 0;
             for (long long t = blockIdx.x; t < ntasks && !*(volatile int*)fail; t += gridDim.x) {
                 const unsigned char *sa, *sb;
