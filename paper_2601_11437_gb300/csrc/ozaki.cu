@@ -52,7 +52,7 @@ __host__ __device__ inline uint32_t oz_off(int p, int row, int k) {
 }
 
 // ------------------------------------------------------------------------------------------
-// slicing: one CTA per tile, thread t handles (row, 8-wide k group) pairs
+// slicing: 4 CTAs per tile (32 operand rows each), thread t handles (row, 8-wide k group) pairs
 //   ROWS = true : operand rows = tile rows, K = tile columns  (A = X, or B = X in C -= A X^T)
 //   ROWS = false: operand rows = tile columns, K = tile rows  (B = X in C -= A X)
 // ------------------------------------------------------------------------------------------
