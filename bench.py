@@ -635,6 +635,10 @@ def main():
         return run_adjoint(args)
     if args.compare_mixed:
         return run_compare(args)
+    if args.precision == "mixed" and args.impl == "native":
+        # the single-field line's roofline counts 28 digit products per tile product; the mixed
+        # path varies that per task, so its single-field measurement is --compare-mixed
+        ap.error("--precision mixed applies to the batched workloads; use --compare-mixed for one field")
     if args.warmup < 3 and args.impl == "native" and not os.environ.get("FBT_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     return run_reference(args) if args.impl == "reference" else run_native(args)
