@@ -1,5 +1,5 @@
 """Pins for the oracle's Algorithm 1 (CPU only): Table 1, the constants of Sec. 2.1, the relaxed
-Armijo test, the 3x3 Fisher solve, and the driver's behaviour on fake evaluators with known
+Armijo test, the 3x3 Fisher solve, and the iteration's behaviour on fake evaluators with known
 answers (one-step convergence on a quadratic, halving, the 60/20 shift rule, singular Fisher,
 infeasible steps), plus a full run on a small field."""
 import math
