@@ -186,7 +186,9 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     sample = (f"oracle Fisher-BT iteration on a seeded {n_sub}-point subsample per step "
               f"({t_sub:.2f} s mean over {args.steps} steps), scaled to n={w.n} by (n/{n_sub})^3")
-    line = {"metric": METRIC, "value": value, "unit": "iters/s", "impl": "reference", "n_gpus": 0,
+    # n_gpus is the launch's N (the line's shape is the native arm's); the oracle itself runs on
+    # rank 0's host cores only, as cpu_baseline records
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sub * scale * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "n": w.n, "theta0": w.theta0},
