@@ -53,6 +53,16 @@ def test_k_against_scipy():
         assert rel(special.bessel_k(v, x), sp.kv(v, x)) < 2e-13   # scipy (Amos) is good to ~1e-14
 
 
+@pytest.mark.parametrize("nu", [0.05, 0.5, 1.2, 2.5, 3.7])
+def test_k_wronskian_with_i(nu):
+    # DLMF 10.28.2: I_nu(x) K_(nu+1)(x) + I_(nu+1)(x) K_nu(x) = 1 / x.  I_nu comes from scipy, an
+    # independent routine; scaled forms (ive e^x, K e^-x cancel) keep large x in range
+    sp = pytest.importorskip("scipy.special")
+    x = XS[(XS >= 1e-4) & (XS <= 400)]
+    lhs = (sp.ive(nu, x) * special.bessel_k(nu + 1, x) + sp.ive(nu + 1, x) * special.bessel_k(nu, x)) * np.exp(x)
+    assert rel(lhs, 1 / x) < 1e-13
+
+
 def test_dnu_at_zero_order_vanishes():
     # K_nu is even in nu, so dK/dnu = 0 at nu = 0
     assert np.all(special.bessel_k_dnu(0.0, XS) == 0.0)
