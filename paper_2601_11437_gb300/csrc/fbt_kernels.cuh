@@ -73,9 +73,11 @@ __host__ __device__ inline long long tile_offset(int i, int j, int T, int nb) {
 }
 __host__ __device__ inline long long num_tiles(int T) { return (long long)T * (T + 1) / 2; }
 
-// linear index t of the lower triangle (row-major: (0,0),(1,0),(1,1),(2,0),...) -> (r, c), c <= r
+// linear index t of the lower triangle (row-major: (0,0),(1,0),(1,1),(2,0),...) -> (r, c), c <= r.
+// The FP32 square root only estimates r (the FP64 pipe is the tile-update epilogue's scarce
+// resource, and every thread decodes every task); the integer steps make the result exact.
 __device__ inline void tri_decode(long long t, int& r, int& c) {
-    long long rr = (long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    long long rr = (long long)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
     while (rr * (rr + 1) / 2 > t) --rr;
     r = (int)rr;
