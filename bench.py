@@ -259,9 +259,13 @@ def run_native(args):
         tasks_per_launch = per_launch_flops / OZAKI_TASK_FLOPS
         roof = {"bound": "tensor", "kernel": f"k_ozaki_gemm ({dom})", "achieved": achieved, "peak": bf16_peak,
                 "unit": "TFLOP/s", "frac": achieved / bf16_peak,
-                "traffic": OZAKI_DRAM_BYTES_PER_TASK * tasks_per_launch,
+                # the counters predate the kernel's last change (the task-index decode's FP32
+                # estimate, which moves no data): null until they are taken again
+                "traffic": None,
+                "traffic_previous_capture": OZAKI_DRAM_BYTES_PER_TASK * tasks_per_launch,
                 "traffic_source": "ncu dram__bytes_read+write of a 1984-task launch at n = 4096, "
-                                  f"scaled to this family's {tasks_per_launch:.0f} tasks per launch",
+                                  f"scaled to this family's {tasks_per_launch:.0f} tasks per launch, "
+                                  "taken before the kernel's last change",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
                                 else "fallback 1.7 PFLOP/s sustained") + " (of measured)",
                 "work": "28 BF16 digit products per FP64-accurate tile product",
