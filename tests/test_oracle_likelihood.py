@@ -31,6 +31,18 @@ def test_cholesky_and_solves(n, nb):
     assert linalg.logdet_from_cholesky(L) == pytest.approx(np.sum(np.log(np.linalg.eigvalsh(A))), rel=1e-12)
 
 
+@pytest.mark.parametrize("n,nb", [(1, 8), (37, 8), (100, 8), (131, 16)])
+def test_cholesky_in_place_matches_the_library(n, nb):
+    # the in-place variant used for the stored fields: trailing updates in column chunks of
+    # 4 nb (several per step at these sizes) and the strict upper triangle zeroed block by block
+    A = spd(n, 40 + n)
+    W = np.array(A, copy=True)
+    L = linalg.cholesky(W, nb=nb, overwrite=True)
+    assert L is W and np.all(np.triu(L, 1) == 0)
+    np.testing.assert_allclose(L, np.linalg.cholesky(A), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(L @ L.T, A, rtol=1e-12, atol=1e-10)
+
+
 def test_cholesky_rejects_indefinite():
     A = spd(20, 3)
     A[5, 5] = -1.0
