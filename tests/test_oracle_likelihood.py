@@ -181,3 +181,20 @@ def test_domain_errors():
         likelihood.loglik(locs, np.zeros(5), (1.0, -0.1, 0.5))
     ev = likelihood.DenseEvaluator(locs, np.zeros(5))
     assert ev.loglik((1.0, 0.1, 0.0)) == -math.inf
+
+
+def test_blocked_covariance_and_field_match_the_dense_ones():
+    # the column-block covariance and in-place factor behind the large stored fields, against
+    # the dense covariance and factor on a size that spans several column blocks
+    n, th = 300, (1.3, 0.12, 0.9)
+    locs = inputs.uniform_locations(n, 17)
+    e = inputs.standard_normal(n, 17)
+    S = matern.covariance(locs, th, partials=False)["S"]
+    Sb = fields.covariance_blocked(locs, th, block=64)
+    np.testing.assert_allclose(Sb, S, rtol=1e-15, atol=0)
+    Sl = fields.covariance_blocked(locs, th, block=64, lower_only=True)
+    low = np.tril_indices(n)
+    np.testing.assert_allclose(Sl[low], S[low], rtol=1e-15, atol=0)
+    z = fields.sample_field(locs, e, th)
+    zb = fields.sample_field_blocked(locs, e, th)
+    np.testing.assert_allclose(zb, z, rtol=1e-9, atol=1e-12 * np.max(np.abs(z)))
