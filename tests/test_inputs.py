@@ -13,6 +13,21 @@ def test_streams_are_deterministic_and_in_range():
     assert abs(e.mean()) < 0.01 and abs(e.std() - 1.0) < 0.01
 
 
+def test_splitmix64_known_answers():
+    # SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) from state 0: the first three outputs of the
+    # published generator, which advances the state by 0x9E3779B97F4A7C15 before each output
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        states = np.array([g * np.uint64(k) for k in (1, 2, 3)], dtype=np.uint64)
+    assert [int(v) for v in inputs._mix64(states)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                       0x06C45D188009454F]
+    # a stream is the generator started from the mixed (seed, stream) key
+    key = int(inputs._mix64(np.array([(5 << 32) | 2], dtype=np.uint64))[0])
+    with np.errstate(over="ignore"):
+        first = inputs._mix64(np.array([np.uint64(key) + g], dtype=np.uint64))[0]
+    assert inputs.random_u64(5, 2, 3)[0] == first
+
+
 def test_batched_recipe_is_a_prefix_of_the_larger_one():
     # the stored 256-field workload is the first 256 fields of the 2,048-field recipe
     small, large = inputs.batched_fields(256), inputs.batched_fields(2048)
