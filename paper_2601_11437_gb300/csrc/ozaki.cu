@@ -379,11 +379,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                     // exact group sums -> fixed point with unit 2^-46 of s_r s_c.  Group g (at
                     // most g + 1 products of digits <= 2^7 over K = 128) is below (g + 1) 2^21 and
                     // carries weight 2^(32 - 8 g) units.  Group 0 (<= 2^21) converts exactly by
-                    // adding 1.5 2^23 in FP32, groups 1..4 with F2I; groups 5, 6 only enter below
-                    // the unit, so adding 1.5 2^25 (ulp 4, round to nearest even) moves the result
-                    // by at most 2^-7 unit.  P = v_g 2^8 + v_(g+1) for g = 0, 2 is exact in 32-bit
-                    // integers (|P23| <= 3 2^29 + 2^23 < 2^31), and the bits below one unit are
-                    // rounded to nearest: the conversion has no bias.
+                    // adding 1.5 2^23 in FP32, groups 1..4 with F2I.  Groups 5, 6 only enter below
+                    // the unit: t56 = v_5 + v_6 / 256 in one FMA (|t56| < 2^24, error <= 1/2 ulp),
+                    // then t56 / 256 + 1.5 2^23 in another rounds their sum to the unit, to
+                    // nearest: at most 1/2 + 2^-9 unit off, without bias.  P = v_g 2^8 + v_(g+1)
+                    // for g = 0, 2 is exact in 32-bit integers (|P23| <= 3 2^29 + 2^23 < 2^31).
                     const int iv0 = __float_as_int(__uint_as_float(v[0][j]) + 12582912.0f) - 0x4B400000;
                     const int iv1 = __float2int_rn(__uint_as_float(v[1][j]));
                     const int iv2 = __float2int_rn(__uint_as_float(v[2][j]));
