@@ -1,18 +1,23 @@
 #!/usr/bin/env python
-"""Fisher-BT benchmark: Fisher-BT iterations per second on one field, FP64 path, on GB300.
+"""Fisher-BT benchmark on GB300: FP64-accurate against mixed precision at matched theta_hat.
 
 A step is one Fisher-BT iteration of Algorithm 1 (Sec. 2.1) over the whole hot path: the
 backtracking line search (Algorithm 2 per candidate: covariance generation, tiled Cholesky,
 log-determinant, triangular solve) followed by the Fisher scoring iteration at the accepted point
-(Algorithm 3: the same plus Sigma_alpha / Sigma_nu generation, back-solve, quadratic forms, the
-two-sided transforms with trace / Frobenius epilogues, assembly) and the 3x3 solve for the next
-direction.  Every timed step starts from the same state (theta^(0) of the workload, its l, score,
-Fisher and direction), so every step does the same work.
+(Algorithm 3: Sigma_alpha / Sigma_nu, back-solve, quadratic forms, the two-sided transforms with
+trace / Frobenius epilogues, assembly) and the 3x3 solve for the next direction.  Every timed step
+starts from the same state (theta^(0) of the workload, its l, score, Fisher and direction), so
+every step does the same work.
+
+The line's value is the FP64-accurate path's iterations/s (tile products from exact BF16 digit
+products on the tensor cores); beside it, in the same line, the mixed path's iterations/s, both
+paths' Fisher-BT estimates from theta^(0) (Algorithm 1 to the paper's stopping rule; the mixed run
+switches to FP64-accurate products once its steps are small) and the Cholesky rate.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload NAME]
 
-Default workload: n = 16,384 uniform locations on [0,1]^2 (seed 1), field z ~ N(0, Sigma) at
-theta_true = (1, 0.1, 1.2) with 1e-8 jitter, start theta^(0) = (0.5, 0.05, 0.8).  N > 1 runs N
+Default workload: n = 65,536 uniform locations on [0,1]^2 (seed 2), field z ~ N(0, Sigma) at
+theta_true = (1, 0.05, 0.8) with 1e-8 jitter, start theta^(0) = (0.7, 0.035, 0.64).  N > 1 runs N
 independent replicas (one per GPU, launched by torchrun); the value is the sum over ranks.
 """
 from __future__ import annotations
@@ -38,18 +43,22 @@ sys.path.insert(0, ROOT)
 from paper_2601_11437_gb300 import inputs  # noqa: E402
 
 FIELDS = os.path.join(ROOT, "tests", "golden", "fields")
-METRIC = "Fisher-BT iterations/s (FP64 path)"
+METRIC = "Fisher-BT iters/s and Cholesky TFLOP/s (% peak): FP64 vs mixed at matched theta_hat"
 PRECISIONS = {"fp64": 0, "fp64_emulated": 1, "mixed": 2}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
-# 1984-task launch at n = 4096 (profiles/k_ozaki_gemm_n4096_full.md: 153.3 MB read + 70.8 MB
-# written); the C tiles, which dominate it, grow in proportion to the tasks
-OZAKI_DRAM_BYTES_PER_TASK = (153.323776e6 + 70.84672e6) / 1984
+# launch of the two-sided transform's trailing update at n = 4096 (read + written bytes over the
+# launch's tasks); the C tiles, which dominate it, grow in proportion to the tasks.  None until a
+# capture of the current kernel exists.
+OZAKI_DRAM_BYTES_PER_TASK = None
 OZAKI_TASK_FLOPS = 2.0 * 128 * 64 * 128
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# subsample sizes of the oracle's timing (CPU baseline and reference arm): its time per iteration
+# is fitted as t(n) = a n^2 + b n^3 (generation O(n^2), dense algebra O(n^3)) and taken to n
+ORACLE_SIZES = (1024, 2048, 4096)
 
 
 def load_field(name: str):
@@ -147,55 +156,130 @@ def cpu_oracle_step_seconds(locs, z, w, n_sub, seed_sub):
     return time.perf_counter() - t0, st.n_ll - st0.n_ll
 
 
-def cpu_baseline(locs, z, w, sizes=(1024, 2048)):
-    """Oracle Fisher-BT iteration at two subsample sizes, extrapolated to the workload's n by
-    t(n) = a n^2 + b n^3 (generation is O(n^2) work, the dense algebra O(n^3))."""
-    ts = []
-    for s in sizes:
-        t, _ = cpu_oracle_step_seconds(locs, z, w, s, 3)
-        ts.append(t)
-    (n1, n2), (t1, t2) = sizes, ts
-    A = np.array([[n1 ** 2, n1 ** 3], [n2 ** 2, n2 ** 3]], dtype=float)
-    a, b = np.linalg.solve(A, np.array([t1, t2]))
-    a, b = max(a, 0.0), max(b, 0.0)
+def oracle_extrapolation(times: dict, n: int):
+    """Least-squares fit t(m) = a m^2 + b m^3 (a, b >= 0) to the oracle's mean iteration time at
+    each measured subsample size m, evaluated at n."""
+    ms = np.array(sorted(times), dtype=float)
+    ts = np.array([np.mean(times[m]) for m in sorted(times)])
+    A = np.stack([ms ** 2, ms ** 3], axis=1)
+    coef, *_ = np.linalg.lstsq(A / ts[:, None], np.ones_like(ts), rcond=None)   # relative residuals
+    a, b = max(coef[0], 0.0), max(coef[1], 0.0)
     if a == 0.0 and b == 0.0:
-        b = t2 / n2 ** 3
-    t_full = a * w.n ** 2 + b * w.n ** 3
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / t_full, "unit": "iters/s", "cores": cores, "kind": "oracle",
-            "sample": (f"one oracle Fisher-BT iteration (numpy FP64; BLAS threads for the matrix "
-                       f"products) on seeded {n1}- and {n2}-point subsamples of the workload "
-                       f"({t1:.1f} s, {t2:.1f} s), extrapolated to n={w.n} by a n^2 + b n^3")}
+        b = float(ts[-1] / ms[-1] ** 3)
+    return a * n ** 2 + b * n ** 3, a, b
+
+
+def cores_used():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(locs, z, w, sizes=ORACLE_SIZES):
+    """The oracle's Fisher-BT iteration at each subsample size once, extrapolated to the
+    workload's n (the reference arm uses the same sizes and rule)."""
+    times = {m: [cpu_oracle_step_seconds(locs, z, w, m, 3)[0]] for m in sizes}
+    t_full, a, b = oracle_extrapolation(times, w.n)
+    meas = ", ".join(f"n={m}: {times[m][0]:.1f} s" for m in sizes)
+    return {"value": 1.0 / t_full, "unit": "iters/s", "cores": cores_used(), "kind": "oracle",
+            "sample": (f"one oracle Fisher-BT iteration (numpy FP64; BLAS threads for the matrix products) "
+                       f"on seeded subsamples of the workload ({meas}), fitted by t = a n^2 + b n^3 "
+                       f"(a = {a:.3e}, b = {b:.3e}) and evaluated at n = {w.n}: {t_full:.0f} s per iteration")}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: Fisher-BT iterations on a bounded subsample, scaled."""
-    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    """The oracle as the reference arm: each step one oracle Fisher-BT iteration on a seeded
+    subsample, the sizes of ORACLE_SIZES in turn; the iterations/s at the workload's n come from
+    the fitted time per iteration, the same rule as the native arm's cpu_baseline."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w, locs, z = load_field(args.workload)
-    n_sub = args.reference_n
-    times = []
-    for i in range(args.warmup + args.steps):
-        t, _ = cpu_oracle_step_seconds(locs, z, w, n_sub, 3)
-        if i >= args.warmup:
-            times.append(t)
-    t_sub = sum(times) / len(times)
-    scale = (w.n / n_sub) ** 3
-    value = 1.0 / (t_sub * scale)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"oracle Fisher-BT iteration on a seeded {n_sub}-point subsample per step "
-              f"({t_sub:.2f} s mean over {args.steps} steps), scaled to n={w.n} by (n/{n_sub})^3")
-    # n_gpus is the launch's N (the line's shape is the native arm's); the oracle itself runs on
-    # rank 0's host cores only, as cpu_baseline records
+    sizes = args.reference_sizes
+    for i in range(args.warmup):
+        cpu_oracle_step_seconds(locs, z, w, sizes[0], 3)
+    times = {m: [] for m in sizes}
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        m = sizes[i % len(sizes)]
+        times[m].append(cpu_oracle_step_seconds(locs, z, w, m, 3)[0])
+    wall = time.perf_counter() - t0
+    times = {m: v for m, v in times.items() if v}
+    if len(times) >= 2:
+        t_full, a, b = oracle_extrapolation(times, w.n)
+        rule = f"fitted by t = a n^2 + b n^3 (a = {a:.3e}, b = {b:.3e})"
+    else:
+        (m, v), = times.items()
+        t_full = float(np.mean(v)) * (w.n / m) ** 3
+        rule = f"scaled by (n/{m})^3"
+    value = 1.0 / t_full
+    meas = ", ".join(f"n={m}: {np.mean(v):.2f} s x {len(v)}" for m, v in sorted(times.items()))
+    sample = (f"oracle Fisher-BT iterations on seeded subsamples, one per step ({meas}), {rule} and "
+              f"evaluated at n = {w.n}: {t_full:.0f} s per iteration")
+    # ms_per_step is the measured time of a step (a subsample iteration); value is the fitted
+    # rate at the full workload, the native arm's unit
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sub * scale * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "n": w.n, "theta0": w.theta0},
-            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "extrapolated_s_per_iteration": t_full,
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fp64_dmma_peak_tflops():
+    """FP64 matrix-multiply rate of this GPU (torch.matmul on float64, the vendor library's DGEMM),
+    the denominator of the Cholesky's "% of FP64 tensor peak"; best of 5 at 8192^3."""
+    import torch
+    a = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    b = torch.randn(8192, 8192, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
+
+
+def timed_steps(fbt, ctx, st0, steps, stream):
+    """`steps` Fisher-BT iterations from the state st0 (each from st0), timed with CUDA events on
+    the context's stream; returns (ms, evaluations, last state)."""
+    import torch
+
+    def one_step():
+        st = fbt.FbtState()
+        ctypes.memmove(ctypes.byref(st), ctypes.byref(st0), ctypes.sizeof(st0))
+        fbt.fisher_bt_step(ctx, st)
+        return st
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    evals, st = 0, None
+    for _ in range(steps):
+        st = one_step()
+        evals += st.n_ll - st0.n_ll
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), evals, st
+
+
+def profiled_step(fbt, ctx, st0):
+    """One Fisher-BT iteration with the library's per-kernel CUDA-event profiler (graphs off)."""
+    st = fbt.FbtState()
+    ctypes.memmove(ctypes.byref(st), ctypes.byref(st0), ctypes.sizeof(st0))
+    fbt.fbt_profile(ctx, True)
+    fbt.fisher_bt_step(ctx, st)
+    prof = fbt.fbt_profile_read(ctx)
+    fbt.fbt_profile(ctx, False)
+    return prof
 
 
 def run_native(args):
@@ -204,89 +288,110 @@ def run_native(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     w, locs, z = load_field(args.workload)
-    prec = PRECISIONS[args.precision]
-    ctx = fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=prec)
+    stream = torch.cuda.current_stream(local)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+
+    # ---- the value: FP64-accurate path, profiler off, graph replay on ----
+    ctx = fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=fbt.PREC_FP64_EMULATED)
     st0 = fbt.fisher_bt_start(ctx, theta0=w.theta0)
     if st0.state != fbt.RUNNING:
         raise RuntimeError(f"start state {st0.state}")
-
-    def one_step(c):
-        st = fbt.FbtState()
-        ctypes.memmove(ctypes.byref(st), ctypes.byref(st0), ctypes.sizeof(st0))
-        fbt.fisher_bt_step(c, st)
-        return st
-
-    for _ in range(args.warmup):
-        one_step(ctx)
-    stream = torch.cuda.current_stream(local)
+    timed_steps(fbt, ctx, st0, args.warmup, stream)
     clocks = Clocks(local)
     barrier(world, local)
     torch.cuda.synchronize()
-    fbt.fbt_profile(ctx, True)
     fbt.fbt_launch_count(ctx, reset=True)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    evals = 0
-    for _ in range(args.steps):
-        st = one_step(ctx)
-        evals += st.n_ll - st0.n_ll
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, evals, _ = timed_steps(fbt, ctx, st0, args.steps, stream)
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
     launches = fbt.fbt_launch_count(ctx)
-    prof = fbt.fbt_profile_read(ctx)
-    fbt.fbt_profile(ctx, False)
     barrier(world, local)
     ms = max_over_ranks(world, ms, local)
     value = world * args.steps / (ms / 1e3)
 
-    # dominant kernel: the tile-update family (FP64 DFMA or emulated-FP64 tensor core) with the
-    # most device time; the library reports FP64-equivalent flops for both
-    gem = {k: v for k, v in prof.items() if k.startswith("gemm") or (k.startswith("ozaki") and k != "ozaki_slice")}
-    w_T = (w.n + args.nb - 1) // args.nb
+    # ---- kernel shares and the dominant kernel's per-launch rate: a separate profiled step ----
+    prof = profiled_step(fbt, ctx, st0)
+    gem = {k: v for k, v in prof.items() if k.startswith("ozaki") and k != "ozaki_slice"}
     dom = max(gem, key=lambda k: gem[k]["ms"])
     per_launch_flops = gem[dom]["flops"] / gem[dom]["launches"]
     per_launch_ms = gem[dom]["ms"] / gem[dom]["launches"]
     fp64eq = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
-    all_gemm_tf = sum(v["flops"] for v in gem.values()) / (sum(v["ms"] for v in gem.values()) * 1e-3) / 1e12
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    if dom.startswith("ozaki"):
-        bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        achieved = fp64eq * OZAKI_PRODUCTS
-        tasks_per_launch = per_launch_flops / OZAKI_TASK_FLOPS
-        roof = {"bound": "tensor", "kernel": f"k_ozaki_gemm ({dom})", "achieved": achieved, "peak": bf16_peak,
-                "unit": "TFLOP/s", "frac": achieved / bf16_peak,
-                # the counters predate the kernel's last change (the task-index decode's FP32
-                # estimate, which moves no data): null until they are taken again
-                "traffic": None,
-                "traffic_previous_capture": OZAKI_DRAM_BYTES_PER_TASK * tasks_per_launch,
-                "traffic_source": "ncu dram__bytes_read+write of a 1984-task launch at n = 4096, "
-                                  f"scaled to this family's {tasks_per_launch:.0f} tasks per launch, "
-                                  "taken before the kernel's last change",
-                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
-                                else "fallback 1.7 PFLOP/s sustained") + " (of measured)",
-                "work": "28 BF16 digit products per FP64-accurate tile product",
-                "fp64_equivalent_tflops": fp64eq}
-    else:
-        roof = {"bound": "alu", "kernel": f"k_gemm_tile ({dom})", "achieved": fp64eq, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": fp64eq / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 DFMA pipe)"}
-    # Cholesky rate: n^3 / 3 per factorisation over the device time of its critical path (on the
-    # emulated path the diagonal tiles are factored on a side stream, overlapped with the updates)
-    if args.precision == "fp64":
-        chol_fams = ("potrf_diag", "trsm_panel", "gemm_potrf_update")
-    else:
-        chol_fams = ("ozaki_potrf_panel", "ozaki_potrf_update", "cholesky_slice")
-    chol_ms = sum(prof[k]["ms"] for k in chol_fams if k in prof)
-    n_chol = prof["potrf_diag"]["launches"] / w_T if "potrf_diag" in prof else 0
-    chol_tf = n_chol * (w.n ** 3 / 3) / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else None
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = fp64eq * OZAKI_PRODUCTS
+    tasks_per_launch = per_launch_flops / OZAKI_TASK_FLOPS
+    roof = {"bound": "tensor", "kernel": f"k_ozaki_gemm ({dom})", "achieved": achieved, "peak": bf16_peak,
+            "unit": "TFLOP/s", "frac": achieved / bf16_peak,
+            "traffic": None if OZAKI_DRAM_BYTES_PER_TASK is None else OZAKI_DRAM_BYTES_PER_TASK * tasks_per_launch,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of this family at "
+                               "n = 4096, per task, times this launch's tasks"
+                               if OZAKI_DRAM_BYTES_PER_TASK is not None else "no capture of the current kernel"),
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks
+                            else "fallback 1.7 PFLOP/s sustained") + " (of measured)",
+            "work": "28 BF16 digit products per FP64-accurate tile product",
+            "per_launch_ms": per_launch_ms, "tasks_per_launch": tasks_per_launch,
+            "fp64_equivalent_tflops": fp64eq}
     total_ms = sum(v["ms"] for v in prof.values())
+    # the Cholesky: n^3 / 3 per factorisation over its critical path on the main stream (the
+    # diagonal tiles are factored and inverted on a side stream beside the trailing updates)
+    chol_fams = ("ozaki_potrf_panel", "ozaki_potrf_update", "cholesky_slice")
+    chol_ms = sum(prof[k]["ms"] for k in chol_fams if k in prof)
+    n_chol = prof["potrf_diag"]["launches"] / ((w.n + args.nb - 1) // args.nb) if "potrf_diag" in prof else 0
+    chol_tf = n_chol * (w.n ** 3 / 3) / (chol_ms * 1e-3) / 1e12 if chol_ms > 0 else None
+    dmma = fp64_dmma_peak_tflops()
+    cholesky = {"tflops_fp64_equivalent": chol_tf, "ms_per_factorisation": chol_ms / max(n_chol, 1),
+                "fp64_matmul_peak_tflops_measured": dmma,
+                "frac_of_fp64_matmul_peak": chol_tf / dmma if chol_tf else None,
+                "bf16_bound_fp64_equivalent_tflops": bf16_peak / OZAKI_PRODUCTS,
+                "frac_of_bf16_bound": chol_tf / (bf16_peak / OZAKI_PRODUCTS) if chol_tf else None,
+                "note": "n^3/3 over the summed device time of the factorisation's main-stream kernels "
+                        "(profiled step); FP64 matmul peak: torch.matmul float64 8192^3 on this GPU"}
 
-    # end to end: every step re-creates the context from pinned host buffers (locations and
-    # field copied host-to-device), runs the iteration, and reads its results back
+    # ---- the mixed path: same workload and start, fewer steps ----
+    mixed = None
+    if not args.no_mixed:
+        cm = fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=fbt.PREC_MIXED, mixed_tol=args.mixed_tol)
+        stm0 = fbt.fisher_bt_start(cm, theta0=w.theta0)
+        km = max(1, min(args.steps, args.mixed_steps))
+        timed_steps(fbt, cm, stm0, min(args.warmup, 3), stream)
+        fbt.fbt_mixed_counts(cm, reset=True)
+        ms_m, evals_m, st_m = timed_steps(fbt, cm, stm0, km, stream)
+        tiers = fbt.fbt_mixed_counts(cm, reset=True)
+        ms_m = max_over_ranks(world, ms_m, local)
+        mixed = {"mixed_tol": args.mixed_tol, "steps": km, "warmup": min(args.warmup, 3),
+                 "iters_per_s": world * km / (ms_m / 1e3), "ms_per_step": ms_m / km,
+                 "speedup_vs_fp64_accurate": (world * km / (ms_m / 1e3)) / value,
+                 "evaluations_per_step": evals_m / km,
+                 "tile_tasks_per_step": {k: v / km for k, v in tiers.items()},
+                 "start_rel_err_vs_fp64_accurate": {
+                     "loglik": abs(stm0.loglik - st0.loglik) / abs(st0.loglik),
+                     "score": (np.abs(np.array(stm0.score[:]) - np.array(st0.score[:]))
+                               / np.abs(np.array(st0.score[:]))).tolist(),
+                     "fisher": (np.abs(np.array(stm0.fisher[:]) - np.array(st0.fisher[:]))
+                                / np.abs(np.array(st0.fisher[:]))).tolist()}}
+        if not args.no_fit:
+            # matched theta_hat: Algorithm 1 from theta^(0) on both paths (wall clock, one each)
+            fits = {}
+            for name, c in (("fp64_accurate", ctx), ("mixed", cm)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fs = fbt.fisher_bt_run(c, theta0=w.theta0)
+                torch.cuda.synchronize()
+                fits[name] = {"seconds": time.perf_counter() - t0, "theta_hat": list(fs.theta), "state": fs.state,
+                              "iterations": fs.iter, "n_ll": fs.n_ll, "n_grad": fs.n_grad,
+                              "grad_norm": float(np.linalg.norm(fs.score[:])), "loglik": fs.loglik}
+                if name == "mixed":
+                    fits[name].update(polish_iter=fs.polish_iter, theta_at_switch=list(fs.theta_mixed))
+            th = np.array(fits["fp64_accurate"]["theta_hat"])
+            rel = lambda v: float(np.max(np.abs(np.array(v) - th) / np.abs(th)))  # noqa: E731
+            mixed["fit"] = fits
+            mixed["theta_hat_rel_err"] = rel(fits["mixed"]["theta_hat"])
+            mixed["theta_at_switch_rel_err"] = rel(fits["mixed"]["theta_at_switch"])
+            mixed["time_to_theta_hat_speedup"] = fits["fp64_accurate"]["seconds"] / fits["mixed"]["seconds"]
+        fbt.fbt_destroy(cm)
+
+    # ---- end to end: every step re-creates the context from pinned host buffers (locations and
+    # field copied host-to-device), runs the iteration and reads its results back ----
     e2e = None
     if not args.no_e2e:
         pl = torch.from_numpy(np.ascontiguousarray(locs)).pin_memory()
@@ -296,7 +401,7 @@ def run_native(args):
         lib = fbt._lib.load()
         opts = fbt.FbtOpts()
         lib.fbt_default_opts(ctypes.byref(opts))
-        opts.nb, opts.device, opts.precision = args.nb, local, prec
+        opts.nb, opts.device, opts.precision = args.nb, local, fbt.PREC_FP64_EMULATED
         nbytes = lib.fbt_workspace_bytes(w.n, ctypes.byref(opts))
         wsp = ctypes.c_void_p((ws.data_ptr() + 255) & ~255)
         h2d = d2h = 0
@@ -305,12 +410,14 @@ def run_native(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             h = ctypes.c_void_p()
-            s = lib.fbt_create(ctypes.byref(h), ctypes.c_void_p(pl.data_ptr()), 0, ctypes.c_void_p(pz.data_ptr()), 0,
-                               w.n, ctypes.byref(opts), wsp, nbytes, ctypes.c_void_p(stream.cuda_stream))
-            if s != 0:
-                raise RuntimeError(f"fbt_create {s}")
+            s_ = lib.fbt_create(ctypes.byref(h), ctypes.c_void_p(pl.data_ptr()), 0, ctypes.c_void_p(pz.data_ptr()), 0,
+                                w.n, ctypes.byref(opts), wsp, nbytes, ctypes.c_void_p(stream.cuda_stream))
+            if s_ != 0:
+                raise RuntimeError(f"fbt_create {s_}")
             c = fbt.Context(h.value, w.n, ws, opts)
-            one_step(c)
+            st = fbt.FbtState()
+            ctypes.memmove(ctypes.byref(st), ctypes.byref(st0), ctypes.sizeof(st0))
+            fbt.fisher_bt_step(c, st)
             hb, db = fbt.fbt_transfer_bytes(c)
             h2d += hb
             d2h += db
@@ -326,27 +433,25 @@ def run_native(args):
     if rank != 0:
         return 0
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(locs, z, w)
+    slab_gb = 3 * 8.0 * ((w.n + args.nb - 1) // args.nb) ** 2 * args.nb ** 2 / 2 / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "nb": args.nb, "theta_true": w.theta_true,
-                   "arithmetic": {"fp64": "FP64 DFMA tile updates",
-                                  "fp64_emulated": "FP64-accurate tile updates from exact BF16 digit products "
-                                                   "on tcgen05 tensor cores (7 x 8-bit balanced slices, FP32 TMEM groups, "
-                                                   "FP64 recombination); all else FP64",
-                                  "mixed": "tile updates from 7, 3 or 1 BF16 digit planes per tile product, chosen "
-                                           "from a bound on the product's entries; diagonal tiles and all else FP64"
-                                  }[args.precision],
                    "theta0": w.theta0, "jitter": w.jitter, "parallelism": f"replicas{world}",
+                   "value_path": "FP64-accurate tile updates from exact BF16 digit products on tcgen05 tensor "
+                                 "cores (7 x 8-bit balanced slices, FP32 TMEM groups, FP64 recombination); "
+                                 "all else FP64; profiler off, graph replay on",
                    "evaluations_per_step": evals / args.steps,
-                   "l2": "no flush: each step streams 3 x 1.1 GB of tile slabs, far above the 129 MB L2"},
+                   "l2": f"no flush: each step streams 3 x {slab_gb / 3:.1f} GB of tile slabs, far above the 129 MB L2"},
+        "mixed": mixed,
+        "cholesky": cholesky,
         "roofline": roof,
-        "cholesky_tflops_fp64_equivalent": chol_tf, "tile_update_tflops_fp64_equivalent": all_gemm_tf,
         "fp64_peak_tflops": FP64_PEAK_TFLOPS,
         "kernel_share": {k: round(v["ms"] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
-        "kernel_share_note": "shares of the summed family times; potrf_diag and trtri_panel run on a side stream, "
-                             "mostly overlapped with the Cholesky's trailing updates",
+        "kernel_share_note": "shares of the summed family times of one profiled step (taken after the timed region); "
+                             "potrf_diag and trtri_panel run on a side stream, mostly overlapped",
         "gpu_launches": launches,
         "clocks": ck,
         "e2e": e2e,
@@ -621,13 +726,18 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="n16384")
+    ap.add_argument("--workload", default="n65536")
     ap.add_argument("--nb", type=int, default=128)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64_emulated")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reference-n", type=int, default=1536)
+    ap.add_argument("--reference-sizes", type=lambda v: [int(x) for x in v.split(",")],
+                    default=list(ORACLE_SIZES), help="oracle subsample sizes of the reference arm")
+    ap.add_argument("--mixed-tol", type=float, default=1e-8, help="tolerance of the mixed path's line entry")
+    ap.add_argument("--mixed-steps", type=int, default=5, help="timed steps of the mixed path (at most --steps)")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fit", action="store_true", help="skip the two Fisher-BT fits (matched theta_hat)")
     ap.add_argument("--threads", type=int, default=16, help="host threads of the batched workload")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
     ap.add_argument("--compare-mixed", action="store_true",
@@ -641,10 +751,11 @@ def main():
         return run_adjoint(args)
     if args.compare_mixed:
         return run_compare(args)
-    if args.precision == "mixed" and args.impl == "native":
-        # the single-field line's roofline counts 28 digit products per tile product; the mixed
-        # path varies that per task, so its single-field measurement is --compare-mixed
-        ap.error("--precision mixed applies to the batched workloads; use --compare-mixed for one field")
+    if args.precision != "fp64_emulated" and args.impl == "native":
+        # the single-field line measures the FP64-accurate path with the mixed path beside it
+        ap.error("--precision applies to the batched, simulation and adjoint modes; the single-field line "
+                 "always measures the FP64-accurate path with the mixed path (--mixed-tol) beside it, "
+                 "and --compare-mixed compares the two in detail")
     if args.warmup < 3 and args.impl == "native" and not os.environ.get("FBT_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     return run_reference(args) if args.impl == "reference" else run_native(args)

@@ -64,9 +64,11 @@ typedef struct {
                           /* largest entries against mixed_tol); the last two need nb = 128.       */
                           /* Diagonal-tile Cholesky, inverses, generation, solves of the field,   */
                           /* the log-determinant and the final reductions stay FP64 throughout.   */
-    double mixed_tol;     /* FBT_PREC_MIXED: a tile product whose largest possible entry stays     */
-                          /* below mixed_tol * sigma^2 * 2^6 uses one plane, below 2^20 times that */
-                          /* three planes; default 1e-12                                           */
+    double mixed_tol;     /* FBT_PREC_MIXED: tau = mixed_tol * sigma^2; a tile product over K =   */
+                          /* 128 whose operand entries are below 2^ea, 2^eb uses 1 plane when      */
+                          /* 2^(ea+eb) < tau / 4, 3 planes when 2^(ea+eb) < 2^13 tau, is skipped   */
+                          /* when 2^(ea+eb) < tau / 2^8 (each keeps the product within tau / 2);   */
+                          /* default 1e-12                                                         */
 } fbt_opts;
 
 enum { FBT_PREC_FP64 = 0, FBT_PREC_FP64_EMULATED = 1, FBT_PREC_MIXED = 2 };
@@ -87,7 +89,8 @@ size_t fbt_workspace_bytes(long long n, const fbt_opts* opts);
  *             owned by the caller and kept alive until fbt_destroy; NULL = the library
  *             allocates (and frees) it itself with cudaMalloc
  *   stream    a cudaStream_t on opts->device, or NULL
- * Locations and field are copied to the device, reordered (Sec. "a0" of the design: Z-order)
+ * Locations and field are copied to the device, put in Z-order (Morton order of the
+ * locations; l, the score and the Fisher matrix are invariant under any reordering of Eq. 1-3)
  * and padded to whole tiles.  On failure *out is NULL.
  */
 fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device,
@@ -129,10 +132,20 @@ fbt_status mle_loglik_grad(fbt_ctx* ctx, const double theta[3], double* loglik, 
 
 /* Options of the Fisher-BT driver (Algorithm 1, Sec. 2.1); fbt_default_bt_opts() fills the
  * paper's values: armijo_c 0.001, rho 0.5, slack 0.001, grad_tol 0.001, max_ll_calls 60,
- * max_grad_calls 20, nm_ftol 1e-9 (plus nm_max_calls 1000, max_halvings 64 as guards). */
+ * max_grad_calls 20, nm_ftol 1e-9 (plus nm_max_calls 1000, max_halvings 64 as guards).
+ * polish_step (default 1e-4; not in the paper) applies to fisher_bt_run on an FBT_PREC_MIXED
+ * context whose tolerance is above 0: the run iterates with the mixed tile products until the
+ * Fisher direction is small, max_i |phi_i / theta_i| <= polish_step, the last line search
+ * halved phi four times or more, or the stopping rule or the shift rule holds on a mixed
+ * evaluation; it then switches the context to all digit planes
+ * (FP64-accurate products), repeats the Fisher scoring iteration at the current theta and
+ * continues Algorithm 1 there, so that the paper's stopping rule is judged on FP64-accurate
+ * values.  The context's tolerance is restored when the run returns.  polish_step < 0 turns the
+ * switch off (the whole run in mixed precision). */
 typedef struct {
     double armijo_c, rho, slack, grad_tol, nm_ftol;
     int max_ll_calls, max_grad_calls, nm_max_calls, max_halvings;
+    double polish_step;
 } fbt_bt_opts;
 
 void fbt_default_bt_opts(fbt_bt_opts* opts);
@@ -140,10 +153,13 @@ void fbt_default_bt_opts(fbt_bt_opts* opts);
 enum { FBT_RUNNING = 0, FBT_CONVERGED = 1, FBT_SHIFT = 2, FBT_DONE_NM = 3, FBT_FAILED = -1 };
 
 /* State of a Fisher-BT run (Algorithm 1): theta^(t), phi^(t) = I^-1 grad l, l, grad l, I at
- * theta^(t), the call counters of the shift rule, the accepted-step count and the state. */
+ * theta^(t), the call counters of the shift rule, the accepted-step count and the state;
+ * halvings of the last line search; polish_iter: the accepted-step count at which a mixed run
+ * switched to FP64-accurate products (-1: no switch), theta_mixed: theta at that switch. */
 typedef struct {
     double theta[3], phi[3], loglik, score[3], fisher[9];
-    int n_ll, n_grad, iter, state, halvings;
+    int n_ll, n_grad, iter, state, halvings, polish_iter;
+    double theta_mixed[3];
 } fbt_state;
 
 /*
@@ -201,12 +217,28 @@ fbt_status fisher_bt_run_batch(fbt_ctx* const* ctxs, int nfields, const double* 
  * or reusing factor and partials), not on theta, which reaches the device through a buffer the
  * sequence itself fills.  The second evaluation of a kind captures its sequence as a CUDA graph;
  * later ones replay it with one launch.  Results are bitwise those of direct launches.  Not
- * used for FBT_PREC_MIXED (its plane thresholds depend on sigma^2) or while profiling.
+ * used for FBT_PREC_MIXED with a tolerance above 0 (its plane thresholds depend on sigma^2) or
+ * while profiling.
  * fbt_set_graphs(ctx, 0) switches to direct launches (and drops the captured graphs).
  */
 fbt_status fbt_set_graphs(fbt_ctx* ctx, int enable);
 /* Number of evaluation kinds currently replayed from a captured graph (0 .. 5). */
 int fbt_graph_count(fbt_ctx* ctx);
+
+/* FBT_PREC_MIXED contexts: set the tolerance of the digit-plane choice (as fbt_opts.mixed_tol;
+ * 0 keeps all 7 planes, the FP64-accurate products of FBT_PREC_FP64_EMULATED, bitwise), read it
+ * back (-1 for a NULL context), and read (optionally reset) the tile-product tasks counted per
+ * tier since creation: counts[0] skipped (every entry below the tolerance), counts[1] 1 plane,
+ * counts[2] 3 planes, counts[3] 7 planes.  FBT_ERR_ARG on other contexts or tol outside [0, 1). */
+fbt_status fbt_set_mixed_tol(fbt_ctx* ctx, double tol);
+double fbt_get_mixed_tol(fbt_ctx* ctx);
+fbt_status fbt_mixed_counts(fbt_ctx* ctx, long long counts[4], int reset);
+
+/* Iteration limit of every mbarrier wait in the tensor-core tile-update kernel (test hook; <= 0
+ * restores the default of 2^26 tries).  A wait that runs out makes the kernel stop issuing work,
+ * wait for the copies and tensor-core operations it already issued, free its tensor memory and
+ * return; the evaluation then fails with FBT_ERR_TIMEOUT and the context stays usable. */
+fbt_status fbt_set_spin_budget(fbt_ctx* ctx, long long iterations);
 
 /* Per-kernel statistics, recorded with CUDA events on the context's stream while enabled. */
 typedef struct {
@@ -265,8 +297,9 @@ fbt_status fbt_generate(fbt_ctx* ctx, const double theta[3], int with_derivative
  *   loglik            host pointer receiving l(theta) (-inf on FBT_ERR_DOMAIN / FBT_ERR_NOT_PD)
  *   stream            cudaStream_t on the current device, or NULL; the call synchronises it
  * Returns FBT_ERR_ARG for n < 1, n > FBT_NOALLOC_MAX_N, NULL pointers or a bad jitter.
- * The first call on a device looks up the array's device address on that device (current at
- * the time of the call); make that first call before any stream capture.  Every call uses the
+ * Every call looks up the array's device address in the current context (the lookup allocates
+ * nothing, and it stays valid after the primary context is reset and created again); make the
+ * first call on a device before any stream capture.  Every call uses the
  * same array and leaves its contents behind for the next; calls whose device work overlaps
  * (two host threads, or two streams not ordered with each other) race on it and must be
  * serialised by the caller.

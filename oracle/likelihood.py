@@ -31,6 +31,10 @@ class Evaluation:
     fisher: np.ndarray         # (3, 3)
     logdet: float
     quad: float                # Z^T Sigma^-1 Z
+    # the two terms of each score component (Eq. 2), l_i = -1/2 trace[i] + 1/2 qform[i]:
+    # trace[i] = tr(Sigma^-1 Sigma_i), qform[i] = w^T Sigma_i w with w = Sigma^-1 Z
+    trace: np.ndarray = None
+    qform: np.ndarray = None
 
 
 def check_theta(theta) -> None:
@@ -72,14 +76,17 @@ def loglik_score_fisher(locs, z, theta, jitter: float = 1e-8, mode: int = 0,
 
     score = np.zeros(3)
     fisher = np.zeros((3, 3))
+    traces, qforms = np.zeros(3), np.zeros(3)
     A = [None, None, None]
     # Step 2 (closed forms, valid in jitter mode 0); mode 1 uses Eq. 2 / Eq. 3 directly
     if mode == 0:
         score[0] = (quad - n) / (2.0 * sigma2)
         fisher[0, 0] = n / (2.0 * sigma2 ** 2)
+        traces[0], qforms[0] = n / sigma2, quad / sigma2
     else:
         A[0] = sigma_inv_times(mats["S_sigma2"])
-        score[0] = -0.5 * np.trace(A[0]) + 0.5 * float(w @ (mats["S_sigma2"] @ w))
+        traces[0], qforms[0] = float(np.trace(A[0])), float(w @ (mats["S_sigma2"] @ w))
+        score[0] = -0.5 * traces[0] + 0.5 * qforms[0]
         fisher[0, 0] = 0.5 * linalg.trace_product(A[0], A[0])
     # Steps 3 and 4
     for i, key in ((1, "S_alpha"), (2, "S_nu")):
@@ -87,14 +94,15 @@ def loglik_score_fisher(locs, z, theta, jitter: float = 1e-8, mode: int = 0,
         A[i] = sigma_inv_times(Si)
         tr = float(np.trace(A[i]))
         v = Si @ w
-        score[i] = -0.5 * tr + 0.5 * float(w @ v)
+        traces[i], qforms[i] = tr, float(w @ v)
+        score[i] = -0.5 * tr + 0.5 * qforms[i]
         if mode == 0:
             fisher[0, i] = fisher[i, 0] = tr / (2.0 * sigma2)
         else:
             fisher[0, i] = fisher[i, 0] = 0.5 * linalg.trace_product(A[0], A[i])
         for j in range(1, i + 1):
             fisher[i, j] = fisher[j, i] = 0.5 * linalg.trace_product(A[i], A[j])
-    return Evaluation(ll, score, fisher, logdet, quad)
+    return Evaluation(ll, score, fisher, logdet, quad, traces, qforms)
 
 
 class DenseEvaluator:

@@ -7,7 +7,7 @@ checksum of the locations it belongs to.
 
     python -m oracle.make_fields n16384
     python -m oracle.make_fields batch2048      (the batched-fields workload, 2048 fields)
-    python -m oracle.make_fields sim20          (the simulation study, 20 realisations each)
+    python -m oracle.make_fields sim50          (the simulation study, 50 realisations each)
 """
 import hashlib
 import json

@@ -304,6 +304,27 @@ def fbt_graph_count(ctx: Context) -> int:
     return int(_lib.load().fbt_graph_count(ctx.handle))
 
 
+def fbt_set_mixed_tol(ctx: Context, tol: float) -> None:
+    """FBT_PREC_MIXED contexts: the digit-plane tolerance (0: all planes, FP64-accurate)."""
+    _check(_lib.load().fbt_set_mixed_tol(ctx.handle, float(tol)), "fbt_set_mixed_tol")
+
+
+def fbt_get_mixed_tol(ctx: Context) -> float:
+    return float(_lib.load().fbt_get_mixed_tol(ctx.handle))
+
+
+def fbt_mixed_counts(ctx: Context, reset: bool = False) -> dict:
+    """Tile-product tasks per tier since creation (or the last reset): skipped, 1, 3, 7 planes."""
+    a = (C.c_longlong * 4)()
+    _check(_lib.load().fbt_mixed_counts(ctx.handle, a, int(bool(reset))), "fbt_mixed_counts")
+    return {"skipped": a[0], "planes1": a[1], "planes3": a[2], "planes7": a[3]}
+
+
+def fbt_set_spin_budget(ctx: Context, iterations: int) -> None:
+    """Test hook: iteration limit of the tensor-core kernel's waits (<= 0: the default)."""
+    _check(_lib.load().fbt_set_spin_budget(ctx.handle, int(iterations)), "fbt_set_spin_budget")
+
+
 def fbt_profile(ctx: Context, enable: bool) -> None:
     _check(_lib.load().fbt_profile(ctx.handle, int(bool(enable))), "fbt_profile")
 

@@ -19,13 +19,15 @@ class FbtOpts(C.Structure):
 class FbtBtOpts(C.Structure):
     _fields_ = [("armijo_c", C.c_double), ("rho", C.c_double), ("slack", C.c_double),
                 ("grad_tol", C.c_double), ("nm_ftol", C.c_double), ("max_ll_calls", C.c_int),
-                ("max_grad_calls", C.c_int), ("nm_max_calls", C.c_int), ("max_halvings", C.c_int)]
+                ("max_grad_calls", C.c_int), ("nm_max_calls", C.c_int), ("max_halvings", C.c_int),
+                ("polish_step", C.c_double)]
 
 
 class FbtState(C.Structure):
     _fields_ = [("theta", C.c_double * 3), ("phi", C.c_double * 3), ("loglik", C.c_double),
                 ("score", C.c_double * 3), ("fisher", C.c_double * 9), ("n_ll", C.c_int),
-                ("n_grad", C.c_int), ("iter", C.c_int), ("state", C.c_int), ("halvings", C.c_int)]
+                ("n_grad", C.c_int), ("iter", C.c_int), ("state", C.c_int), ("halvings", C.c_int),
+                ("polish_iter", C.c_int), ("theta_mixed", C.c_double * 3)]
 
 
 class FbtKernelStat(C.Structure):
@@ -59,6 +61,10 @@ SIGNATURES = {
                                       C.POINTER(FbtBtOpts), C.POINTER(FbtState), C.POINTER(C.c_int), C.c_int]),
     "fbt_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_graph_count": (C.c_int, [C.c_void_p]),
+    "fbt_set_mixed_tol": (C.c_int, [C.c_void_p, C.c_double]),
+    "fbt_get_mixed_tol": (C.c_double, [C.c_void_p]),
+    "fbt_mixed_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
+    "fbt_set_spin_budget": (C.c_int, [C.c_void_p, C.c_longlong]),
     "fbt_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(FbtKernelStat), C.c_int, C.POINTER(C.c_int)]),
     "fbt_launch_count": (C.c_longlong, [C.c_void_p, C.c_int]),

@@ -132,6 +132,9 @@ struct fbt_ctx {
     unsigned char* wcs = nullptr;            // their digit planes, column-sliced
     double* yscratch = nullptr;              // two scratch tiles
     double* vx = nullptr;                    // one solved block of a triangular solve
+    unsigned long long* tier_counts = nullptr;   // mixed path: tasks per tier (device, 4)
+    double mixed_tol = 0.0;                  // mixed path: the current tolerance (0: all planes)
+    long long spin_budget = 0;               // mbarrier wait limit of the tensor-core kernel (0: default)
     Profiler* prof = nullptr;
     long long launches = 0;
     long long h2d_bytes = 0, d2h_bytes = 0;
@@ -168,6 +171,9 @@ static fbt_status cuda_fail(cudaError_t e, const char* where) {
     tl_cuda_error = std::string(where) + ": " + cudaGetErrorString(e);
     return FBT_ERR_CUDA;
 }
+namespace fbt {
+fbt_status record_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+}  // namespace fbt
 #define CK(call, where)                                              \
     do {                                                             \
         cudaError_t e_ = (call);                                     \
@@ -205,6 +211,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pdg = take((size_t)T * ns * 5 * 8);
     char* pod = take((size_t)tiles * ns * 3 * 8);
     char* pst = take(sizeof(int) * 4);
+    char* ptier = take(4 * sizeof(unsigned long long));
     char* pout = take(sizeof(EvalOut));
     char* pS = take(slab);
     char* pSA = o.with_derivatives ? take(slab) : nullptr;
@@ -238,6 +245,7 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
         c->slots.logdet = (double*)pld; c->slots.qform = (double*)pqf;
         c->slots.diag = (double*)pdg; c->slots.offd = (double*)pod;
         c->status = (int*)pst; c->out = (EvalOut*)pout;
+        c->tier_counts = (unsigned long long*)ptier;
         c->S = (double*)pS; c->SA = (double*)pSA; c->SN = (double*)pSN;
     }
     return off;
@@ -277,6 +285,7 @@ static Launcher launcher(fbt_ctx* c) {
     L.stream = c->stream;
     L.prof = c->prof;
     L.launches = &c->launches;
+    L.spin = c->spin_budget;
     return L;
 }
 
@@ -316,6 +325,7 @@ fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device, con
         c->ws_bytes = need;
     }
     carve(n, o, c->ws, c);
+    c->mixed_tol = o.precision == FBT_PREC_MIXED ? o.mixed_tol : 0.0;
     {
         void* pin = nullptr;
         if (cudaHostAlloc(&pin, 4 * sizeof(double) + sizeof(EvalOut), cudaHostAllocDefault) != cudaSuccess) {
@@ -351,6 +361,8 @@ fbt_status fbt_create(fbt_ctx** out, const double* locs, int locs_on_device, con
                             z_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) { st = cuda_fail(e, "copy field"); break; }
         c->h2d_bytes += (locs_on_device ? 0 : 16ll * n) + (z_on_device ? 0 : 8ll * n);
+        e = cudaMemsetAsync(c->tier_counts, 0, 4 * sizeof(unsigned long long), c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "clear counters"); break; }
         Launcher L = launcher(c);
         int rc = launch_reorder(L, raw_locs, raw_z, n, c->g.npad, o.reorder, keys, c->bbox, c->X,
                                 c->Y, c->Z, c->perm);
@@ -412,6 +424,26 @@ struct EvalFlags {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
+// The digit-plane thresholds of the mixed path at theta.  With tau = mixed_tol * sigma^2 and a
+// tile product C -= A B^T over K = 128 whose operand entries are below 2^ea and 2^eb (e = ea + eb):
+//   * 1 plane (8-bit digits, truncation below 2^-8 of each row's scale) errs by at most
+//     2 * 128 * 2^-8 * 2^e = 2^e per entry: used when e < floor(log2 tau) - 1;
+//   * 3 planes (24 bits) err by at most 2^(e - 16): used when e < floor(log2 tau) + 13;
+//   * every entry of the product is below 128 * 2^e: skipped when e < floor(log2 tau) - 7.
+// So every tile product is computed to within tau / 2 of its exact value.  mixed_tol = 0 (the
+// polish phase of Algorithm 1) keeps all 7 planes: the emulated-FP64 arithmetic exactly.
+static MixedPolicy mixed_policy(const fbt_ctx* c, const double theta[3]) {
+    MixedPolicy pol;
+    if (c->opts.precision != FBT_PREC_MIXED || !(c->mixed_tol > 0.0)) return pol;
+    const int l2 = (int)floor(log2(c->mixed_tol * theta[0]));
+    pol.on = 1;
+    pol.e_skip = l2 - 7;
+    pol.e_fp32 = l2 - 1;
+    pol.e_fp64 = l2 + 13;
+    pol.counts = c->tier_counts;
+    return pol;
+}
+
 // Enqueue the device work of one evaluation on c->stream (no host synchronisation).
 static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy& pol) {
     Launcher L = launcher(c);
@@ -452,7 +484,7 @@ static fbt_status enqueue_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy
 // captured graph from then on.  A capture that fails switches the context to direct launches.
 static fbt_status run_eval(fbt_ctx* c, const EvalFlags& f, const MixedPolicy& pol) {
     const int v = f.variant();
-    const bool graphable = c->graphs && !c->prof && c->opts.precision != FBT_PREC_MIXED;
+    const bool graphable = c->graphs && !c->prof && !pol.on;
     if (graphable && c->gseen[v] >= 1 && !c->gexec[v]) {
         const long long before = c->launches;
         fbt_status est = FBT_OK;
@@ -504,17 +536,7 @@ static fbt_status evaluate(fbt_ctx* c, const double theta[3], bool deriv, bool k
     const EvalFlags f{deriv, reuse, have_partials, gen_partials};
     c->factor_valid = false;
     if (deriv || gen_partials) c->partials_valid = false;     // SA, SN are about to change
-    MixedPolicy pol;
-    if (c->opts.precision == FBT_PREC_MIXED) {
-        // a tile product whose largest possible entry is below tol * sigma^2 * 2^6 may use one
-        // 8-bit digit plane, below tol * sigma^2 * 2^20 three planes (see MixedPolicy); the
-        // thresholds were set for 7-bit digits and keep a factor 2 (one plane) to 2^3 (three)
-        // of margin with 8-bit ones
-        const double l2 = log2(c->opts.mixed_tol * theta[0]);
-        pol.on = 1;
-        pol.e_fp32 = (int)floor(l2) - 1;
-        pol.e_fp64 = (int)floor(l2) + 13;
-    }
+    const MixedPolicy pol = mixed_policy(c, theta);
     for (int i = 0; i < 3; ++i) c->pin_theta[i] = theta[i];
     c->pin_theta[3] = c->opts.jitter;
     if (reuse) c->factor_reuses += 1;
@@ -547,13 +569,7 @@ static fbt_status evaluate_adjoint(fbt_ctx* c, const double theta[3]) {
     const bool reuse = c->factor_valid && same_theta(theta, c->factor_theta);
     c->factor_valid = false;
     c->partials_valid = false;            // SA, SN receive L^-1 and Sigma^-1
-    MixedPolicy pol;
-    if (c->opts.precision == FBT_PREC_MIXED) {
-        const double l2 = log2(c->opts.mixed_tol * theta[0]);
-        pol.on = 1;
-        pol.e_fp32 = (int)floor(l2) - 1;
-        pol.e_fp64 = (int)floor(l2) + 13;
-    }
+    const MixedPolicy pol = mixed_policy(c, theta);
     if ((rc = launch_prep_theta(L, theta, c->opts.jitter, c->tc, c->qt))) return cuda_fail((cudaError_t)rc, "prep_theta");
     if (reuse) {
         c->factor_reuses += 1;
@@ -698,6 +714,53 @@ int fbt_graph_count(fbt_ctx* c) {
     return k;
 }
 
+fbt_status fbt_set_mixed_tol(fbt_ctx* c, double tol) {
+    if (!c || c->opts.precision != FBT_PREC_MIXED || !(tol >= 0.0 && tol < 1.0)) return FBT_ERR_ARG;
+    if (tol == c->mixed_tol) return FBT_OK;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->stream), "mixed_tol sync");
+    // graphs captured under the previous policy would replay it: drop them
+    for (int v = 0; v < 5; ++v) {
+        if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
+        c->gexec[v] = nullptr;
+        c->gseen[v] = 0;
+    }
+    c->mixed_tol = tol;
+    // the kept factor and partials were computed under the previous policy
+    c->factor_valid = false;
+    c->partials_valid = false;
+    return FBT_OK;
+}
+
+double fbt_get_mixed_tol(fbt_ctx* c) { return c ? c->mixed_tol : -1.0; }
+
+fbt_status fbt_set_spin_budget(fbt_ctx* c, long long iterations) {
+    if (!c) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(c->stream), "spin budget sync");
+    for (int v = 0; v < 5; ++v) {           // captured graphs carry the old budget
+        if (c->gexec[v]) cudaGraphExecDestroy(c->gexec[v]);
+        c->gexec[v] = nullptr;
+        c->gseen[v] = 0;
+    }
+    c->spin_budget = iterations > 0 ? iterations : 0;
+    return FBT_OK;
+}
+
+fbt_status fbt_mixed_counts(fbt_ctx* c, long long counts[4], int reset) {
+    if (!c || !counts) return FBT_ERR_ARG;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, c->tier_counts, sizeof h, cudaMemcpyDeviceToHost, c->stream), "read counters");
+    CK(cudaStreamSynchronize(c->stream), "counters sync");
+    for (int i = 0; i < 4; ++i) counts[i] = (long long)h[i];
+    if (reset) {
+        CK(cudaMemsetAsync(c->tier_counts, 0, sizeof h, c->stream), "clear counters");
+        CK(cudaStreamSynchronize(c->stream), "counters sync");
+    }
+    return FBT_OK;
+}
+
 fbt_status fbt_profile(fbt_ctx* c, int enable) {
     if (!c) return FBT_ERR_ARG;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -791,5 +854,6 @@ cudaStream_t ctx_swap_stream(fbt_ctx* c, cudaStream_t s) {
     return prev;
 }
 int ctx_device(const fbt_ctx* c) { return c->device; }
+bool ctx_is_mixed(const fbt_ctx* c) { return c->opts.precision == FBT_PREC_MIXED; }
 long long ctx_n(const fbt_ctx* c) { return c->g.n; }
 }  // namespace fbt

@@ -24,10 +24,13 @@ enum : int { PREC_FP64 = 0, PREC_FP64_OZAKI = 1, PREC_MIXED = 2 };
 
 // Mixed path: a tile product with operand maxima 2^ea, 2^eb uses all 7 digit planes
 // (FP64-accurate) if ea + eb >= e_fp64, 3 planes (24 bits, FP32-class) if ea + eb >= e_fp32,
-// else 1 plane (8 bits, BF16-class); the thresholds follow from mixed_tol * sigma^2.
+// 1 plane (8 bits, BF16-class) if ea + eb >= e_skip, and is skipped (its entries are all below
+// the tolerance) otherwise; the thresholds follow from mixed_tol * sigma^2.  counts (optional,
+// device): tasks per tier (skipped, 1, 3, 7 planes), accumulated over launches.
 struct MixedPolicy {
     int on = 0;
-    int e_fp64 = 0, e_fp32 = 0;
+    int e_fp64 = 0, e_fp32 = 0, e_skip = -100000;
+    unsigned long long* counts = nullptr;
 };
 
 // ---- trapezoid quadrature of K_nu, K_{nu-1} and dK_nu/dnu (see matern_gen.cu) ----
@@ -121,6 +124,8 @@ struct OzGemmJob {
     int assign;                    // 1: C = -mult * A B^T (overwrite); 0: C -= mult * A B^T
     int mixed = 0;                 // 1: digit planes per task from the operand magnitudes
     int e_fp64 = 0, e_fp32 = 0;    // exponent thresholds of the mixed path (see task_planes)
+    int e_skip = -100000;
+    unsigned long long* counts = nullptr;   // tasks per tier (mixed path, optional)
     __device__ void task(long long bid, const unsigned char*& sa, const unsigned char*& sb,
                          double*& Ct, int& c0, double& m) const {
         const long long tsk = bid >> 1;
@@ -183,6 +188,7 @@ struct Launcher {
     cudaStream_t stream = nullptr;
     Profiler* prof = nullptr;        // non-null while profiling is enabled
     long long* launches = nullptr;   // running count of this library's kernel launches
+    long long spin = 0;              // iteration limit of the tensor-core kernel's waits (0: default)
     int family = -1;
     int launches_in_group = 0;
     void begin(const char* family_name);

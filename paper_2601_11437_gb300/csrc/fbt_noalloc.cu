@@ -8,9 +8,9 @@
 // file-scope device array of fixed size, allocated once when the library is loaded and held by
 // every GPU that loads it until the process exits.  It runs the same kernels as mle_loglik.
 #include <math.h>
-#include <mutex>
 
 #include "../../include/fbt.h"
+#include "fbt_ctx_access.h"
 #include "fbt_kernels.cuh"
 
 using namespace fbt;
@@ -22,11 +22,23 @@ constexpr size_t NA_SCRATCH_BYTES = 5u << 20;     // 5 MiB, enough for n <= FBT_
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_SCRATCH_BYTES];
 
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[NA_MAX_DEVICES] = {nullptr};
+constexpr size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
+// Bytes of the loglik-only workspace for n points, in the order carve_noalloc takes them
+// (constexpr, so that the size bound of FBT_NOALLOC_MAX_N is checked at compile time).
+constexpr size_t noalloc_bytes(long long n) {
+    const long long T = (n + NA_NB - 1) / NA_NB;
+    const size_t npad = (size_t)(T * NA_NB);
+    const size_t tiles = (size_t)(T * (T + 1) / 2);
+    size_t off = 0;
+    const size_t parts[12] = {npad * 8, npad * 8, npad * 8, npad * 8, (size_t)n * 8, 4 * 8,
+                              sizeof(ThetaConsts), sizeof(QuadTables), (size_t)T * 8, 4 * sizeof(int),
+                              sizeof(EvalOut), tiles * NA_NB * NA_NB * 8};
+    for (size_t b : parts) off = a256(off + b);
+    return off;
+}
+static_assert(noalloc_bytes(FBT_NOALLOC_MAX_N) <= NA_SCRATCH_BYTES,
+              "the scratch array must hold the workspace of FBT_NOALLOC_MAX_N points");
 
 struct NoallocLayout {
     double *X, *Y, *Z, *vy, *bbox;
@@ -40,7 +52,7 @@ struct NoallocLayout {
     size_t bytes;
 };
 
-// Carves the loglik-only workspace for n points out of base (base may be null to size it).
+// Carves the loglik-only workspace for n points out of base (same order as noalloc_bytes).
 NoallocLayout carve_noalloc(long long n, char* base) {
     const long long T = (n + NA_NB - 1) / NA_NB;
     const long long npad = T * NA_NB;
@@ -64,17 +76,15 @@ NoallocLayout carve_noalloc(long long n, char* base) {
     return L;
 }
 
-// Device address of the scratch array on the current device (set up once per device).
-fbt_status scratch_address(int dev, void** ptr) {
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return FBT_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return FBT_ERR_CUDA;
-        g_noalloc_ptr[dev] = p;
-    }
-    *ptr = g_noalloc_ptr[dev];
+// Device address of the scratch array in the current context.  It is looked up on every call,
+// not cached: the lookup allocates nothing, and a cached address would be stale after the
+// primary context is torn down and created again (cudaDeviceReset), when the module is reloaded.
+fbt_status scratch_address(void** ptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return record_cuda_error(e, "noalloc scratch address");
+    if (!p) return record_cuda_error(cudaErrorInvalidSymbol, "noalloc scratch address");
+    *ptr = p;
     return FBT_OK;
 }
 
@@ -94,10 +104,8 @@ fbt_status fbt_loglik_noalloc(const double* locs, const double* z, int inputs_on
         *loglik = -INFINITY;
         return FBT_ERR_DOMAIN;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FBT_ERR_CUDA;
     void* base = nullptr;
-    fbt_status st = scratch_address(dev, &base);
+    fbt_status st = scratch_address(&base);
     if (st != FBT_OK) return st;
     NoallocLayout W = carve_noalloc(n, (char*)base);
     if (W.bytes > NA_SCRATCH_BYTES) return FBT_ERR_ARG;
@@ -114,22 +122,32 @@ fbt_status fbt_loglik_noalloc(const double* locs, const double* z, int inputs_on
     double* raw_locs = (double*)(keys + npow2);
     double* raw_z = raw_locs + 2 * n;
     const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpyAsync(raw_locs, locs, (size_t)n * 16, kind, s) != cudaSuccess) return FBT_ERR_CUDA;
-    if (cudaMemcpyAsync(raw_z, z, (size_t)n * 8, kind, s) != cudaSuccess) return FBT_ERR_CUDA;
+    cudaError_t e;
+    int rc;
+    if ((e = cudaMemcpyAsync(raw_locs, locs, (size_t)n * 16, kind, s)) != cudaSuccess)
+        return record_cuda_error(e, "noalloc copy locations");
+    if ((e = cudaMemcpyAsync(raw_z, z, (size_t)n * 8, kind, s)) != cudaSuccess)
+        return record_cuda_error(e, "noalloc copy field");
     // the array keeps the previous call's contents: the status word must start at zero
-    if (cudaMemsetAsync(W.status, 0, sizeof(int), s) != cudaSuccess) return FBT_ERR_CUDA;
+    if ((e = cudaMemsetAsync(W.status, 0, sizeof(int), s)) != cudaSuccess)
+        return record_cuda_error(e, "noalloc clear status");
     Launcher L;
     L.stream = s;
-    if (launch_reorder(L, raw_locs, raw_z, n, g.npad, 1, keys, W.bbox, W.X, W.Y, W.Z, W.perm)) return FBT_ERR_CUDA;
-    if (launch_prep_theta(L, theta, jitter, W.tc, W.qt)) return FBT_ERR_CUDA;
-    if (launch_generate(L, g, W.X, W.Y, W.tc, W.qt, W.S, nullptr, nullptr, false, W.status)) return FBT_ERR_CUDA;
-    if (launch_potrf(L, g, W.S, W.slots.logdet, W.status)) return FBT_ERR_CUDA;
-    if (cudaMemcpyAsync(W.vy, W.Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return FBT_ERR_CUDA;
-    if (launch_trsv(L, g, W.S, W.vy, false)) return FBT_ERR_CUDA;
-    if (launch_assemble(L, g, W.vy, W.slots, false, W.tc, W.status, W.out)) return FBT_ERR_CUDA;
+    if ((rc = launch_reorder(L, raw_locs, raw_z, n, g.npad, 1, keys, W.bbox, W.X, W.Y, W.Z, W.perm)))
+        return record_cuda_error((cudaError_t)rc, "noalloc reorder");
+    if ((rc = launch_prep_theta(L, theta, jitter, W.tc, W.qt))) return record_cuda_error((cudaError_t)rc, "noalloc prep_theta");
+    if ((rc = launch_generate(L, g, W.X, W.Y, W.tc, W.qt, W.S, nullptr, nullptr, false, W.status)))
+        return record_cuda_error((cudaError_t)rc, "noalloc generate");
+    if ((rc = launch_potrf(L, g, W.S, W.slots.logdet, W.status))) return record_cuda_error((cudaError_t)rc, "noalloc potrf");
+    if ((e = cudaMemcpyAsync(W.vy, W.Z, (size_t)g.npad * 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return record_cuda_error(e, "noalloc copy field to solve vector");
+    if ((rc = launch_trsv(L, g, W.S, W.vy, false))) return record_cuda_error((cudaError_t)rc, "noalloc trsv");
+    if ((rc = launch_assemble(L, g, W.vy, W.slots, false, W.tc, W.status, W.out)))
+        return record_cuda_error((cudaError_t)rc, "noalloc assemble");
     EvalOut host{};
-    if (cudaMemcpyAsync(&host, W.out, sizeof(EvalOut), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FBT_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return FBT_ERR_CUDA;
+    if ((e = cudaMemcpyAsync(&host, W.out, sizeof(EvalOut), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return record_cuda_error(e, "noalloc copy result");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return record_cuda_error(e, "noalloc synchronize");
     if (host.status & ST_NOT_PD) { *loglik = -INFINITY; return FBT_ERR_NOT_PD; }
     if (host.status & ST_BESSEL) { *loglik = -INFINITY; return FBT_ERR_BESSEL; }
     *loglik = host.loglik;

@@ -187,6 +187,7 @@ void fbt_default_bt_opts(fbt_bt_opts* o) {
     o->max_grad_calls = 20;
     o->nm_max_calls = 1000;
     o->max_halvings = 64;
+    o->polish_step = 1e-4;
 }
 
 fbt_status fisher_bt_start(fbt_ctx* ctx, const double* theta0, const double* lo, const double* hi,
@@ -197,6 +198,7 @@ fbt_status fisher_bt_start(fbt_ctx* ctx, const double* theta0, const double* lo,
     if (bto) bt = *bto;
     memset(st, 0, sizeof *st);
     st->loglik = -INFINITY;
+    st->polish_iter = -1;
     if (theta0) {
         memcpy(st->theta, theta0, 3 * sizeof(double));
     } else {
@@ -245,38 +247,94 @@ fbt_status fisher_bt_step(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts* bto) {
     return fisher_iteration(ctx, st, bt);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The mixed phase of a run on an FBT_PREC_MIXED context ends when the Fisher direction is small
+// against theta, when the stopping or the shift rule holds on a mixed evaluation, or when the
+// last line search halved four times or more (the mixed l may then be too coarse for the
+// Armijo slack of 0.001).
+bool mixed_phase_done(const fbt_state* st, const fbt_bt_opts& bt) {
+    if (st->state != FBT_RUNNING) return true;
+    if (st->iter > 0 && st->halvings >= 4) return true;
+    double rel = 0.0;
+    for (int d = 0; d < 3; ++d) rel = fmax(rel, fabs(st->phi[d]) / fabs(st->theta[d]));
+    return rel <= bt.polish_step;
+}
+
+fbt_status run_steps(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts& bt, bool mixed_phase) {
+    for (int i = 0; i < 200 && st->state == FBT_RUNNING; ++i) {
+        if (mixed_phase && mixed_phase_done(st, bt)) return FBT_OK;
+        fbt_status s = fisher_bt_step(ctx, st, &bt);
+        if (s != FBT_OK) return s;
+    }
+    return FBT_OK;
+}
+
+fbt_status run_algorithm1(fbt_ctx* ctx, const double* theta0, const double* lo, const double* hi,
+                          const fbt_bt_opts& bt, fbt_state* st) {
+    const double tol0 = fbt_get_mixed_tol(ctx);
+    const bool polish = fbt::ctx_is_mixed(ctx) && tol0 > 0.0 && bt.polish_step >= 0.0;
+    fbt_status s = fisher_bt_start(ctx, theta0, lo, hi, &bt, st);
+    if (s != FBT_OK) return s;
+    if (polish) {
+        // mixed phase; a failed line search (FBT_FAILED) ends the run as on any context
+        if ((s = run_steps(ctx, st, bt, true)) != FBT_OK) return s;
+        if (st->state == FBT_FAILED) return FBT_OK;
+        // polish: FP64-accurate products from here on, starting with the Fisher scoring
+        // iteration at the current theta
+        st->polish_iter = st->iter;
+        memcpy(st->theta_mixed, st->theta, sizeof st->theta);
+        if ((s = fbt_set_mixed_tol(ctx, 0.0)) != FBT_OK) return s;
+        st->state = FBT_RUNNING;
+        if ((s = fisher_iteration(ctx, st, bt)) != FBT_OK) return s;
+    }
+    return run_steps(ctx, st, bt, false);
+}
+
+// Nelder-Mead from the current theta, then one Fisher evaluation at its result (Sec. 2.1).
+fbt_status nelder_mead_phase(fbt_ctx* ctx, fbt_state* st, const fbt_bt_opts& bt) {
+    NegLL f{ctx};
+    double th[3];
+    const int calls = nelder_mead(f, st->theta, th, bt);
+    st->n_ll += calls;
+    if (f.err != FBT_OK) return f.err;
+    memcpy(st->theta, th, sizeof th);
+    double ll, g[3], I[9];
+    const fbt_status s = mle_eval(ctx, th, &ll, g, I);
+    st->n_ll += 1;
+    st->n_grad += 1;
+    if (s != FBT_OK) {
+        st->state = FBT_FAILED;
+        return hard_error(s) ? s : FBT_OK;
+    }
+    st->loglik = ll;
+    memcpy(st->score, g, sizeof g);
+    memcpy(st->fisher, I, sizeof I);
+    st->state = FBT_DONE_NM;
+    return FBT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 fbt_status fisher_bt_run(fbt_ctx* ctx, const double* theta0, const double* lo, const double* hi,
                          const fbt_bt_opts* bto, fbt_state* st) {
     fbt_bt_opts bt;
     fbt_default_bt_opts(&bt);
     if (bto) bt = *bto;
-    fbt_status s = fisher_bt_start(ctx, theta0, lo, hi, &bt, st);
-    if (s != FBT_OK) return s;
-    for (int i = 0; i < 200 && st->state == FBT_RUNNING; ++i) {
-        s = fisher_bt_step(ctx, st, &bt);
-        if (s != FBT_OK) return s;
+    if (!ctx || !st) return FBT_ERR_ARG;
+    const double tol0 = fbt_get_mixed_tol(ctx);
+    fbt_status s = run_algorithm1(ctx, theta0, lo, hi, bt, st);
+    if (s == FBT_OK && st->state == FBT_SHIFT) s = nelder_mead_phase(ctx, st, bt);
+    // a polished mixed run leaves the context at the tolerance it had
+    if (fbt::ctx_is_mixed(ctx) && fbt_get_mixed_tol(ctx) != tol0) {
+        const fbt_status r = fbt_set_mixed_tol(ctx, tol0);
+        if (s == FBT_OK) s = r;
     }
-    if (st->state == FBT_SHIFT) {
-        NegLL f{ctx};
-        double th[3];
-        const int calls = nelder_mead(f, st->theta, th, bt);
-        st->n_ll += calls;
-        if (f.err != FBT_OK) return f.err;
-        memcpy(st->theta, th, sizeof th);
-        double ll, g[3], I[9];
-        s = mle_eval(ctx, th, &ll, g, I);
-        st->n_ll += 1;
-        st->n_grad += 1;
-        if (s != FBT_OK) {
-            st->state = FBT_FAILED;
-            return hard_error(s) ? s : FBT_OK;
-        }
-        st->loglik = ll;
-        memcpy(st->score, g, sizeof g);
-        memcpy(st->fisher, I, sizeof I);
-        st->state = FBT_DONE_NM;
-    }
-    return FBT_OK;
+    return s;
 }
 
 }  // extern "C"

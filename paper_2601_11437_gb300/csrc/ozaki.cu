@@ -39,7 +39,10 @@ constexpr int OZ_STAGE_A = OZ_S * OZ_CHUNK;                  // 28 KB
 constexpr int OZ_STAGE_B = OZ_S * (OZ_N * OZ_KC * 2);        // 14 KB
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_SMEM = OZ_STAGES * (OZ_STAGE_A + OZ_STAGE_B) + 1024;   // 169 KB
-constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits
+constexpr long long OZ_SPIN_LIMIT = 1ll << 26;               // bounded mbarrier waits (default)
+// After a wait has run out, the roles wait (with this budget) for the bulk copies and MMAs they
+// already issued before the CTA frees its tensor memory and exits.
+constexpr long long OZ_DRAIN_LIMIT = 1ll << 26;
 
 size_t ozaki_tile_bytes() { return OZ_TILE_BYTES + 128 * sizeof(double); }   // digits + row exponents
 
@@ -152,9 +155,9 @@ __device__ inline uint64_t oz_desc(uint32_t saddr) {
 __device__ inline void mbar_init(uint64_t* b, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
 }
-__device__ inline bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ inline bool mbar_wait(uint64_t* b, uint32_t parity, long long limit) {
     uint32_t done = 0;
-    for (long long it = 0; it < OZ_SPIN_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(smem_u32(b)), "r"(parity) : "memory");
         if (done) return true;
@@ -216,16 +219,33 @@ constexpr int OZ_EPI_WARPS = 16;                        // 4 per TMEM lane quart
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_EPI_COLS = OZ_N * 4 / OZ_EPI_WARPS;   // accumulator columns per epilogue warp
 
-// Digit planes used for a task: 7 (FP64-accurate); in the mixed path 3 or 1 when the operand
-// tiles' largest entries, 2^ea and 2^eb, make the product small against the thresholds.
-__device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa, const unsigned char* sb) {
+// Digit planes used for a task: 7 (FP64-accurate); in the mixed path 3, 1 or 0 (skipped) when
+// the operand tiles' largest entries, 2^ea over the task's 128 A rows and 2^eb over its 64 B rows
+// (output columns c0 .. c0 + 63), make the product small against the thresholds.
+__device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa, const unsigned char* sb, int c0) {
     if (!job.mixed) return OZ_S;
     const int* ha = (const int*)(sa + OZ_TILE_BYTES) + 128;
-    const int* hb = (const int*)(sb + OZ_TILE_BYTES) + 128;
+    const int* hb = (const int*)(sb + OZ_TILE_BYTES) + 128 + (c0 >> 5);
     const int ea = max(max(ha[0], ha[1]), max(ha[2], ha[3]));
-    const int eb = max(max(hb[0], hb[1]), max(hb[2], hb[3]));
+    const int eb = max(hb[0], hb[1]);
     const int e = ea + eb;
-    return e >= job.e_fp64 ? OZ_S : (e >= job.e_fp32 ? 3 : 1);
+    return e >= job.e_fp64 ? OZ_S : (e >= job.e_fp32 ? 3 : (e >= job.e_skip ? 1 : 0));
+}
+
+// The MMAs of one K stage for NP digit planes: the products A_p B_q with p + q < NP, stacked
+// as (p, q0 .. q0 + 3) into one MMA of N = 64 (q1 - q0 + 1) (see the MMA warp below).
+template <int NP>
+__device__ inline void issue_stage(uint32_t tmem, uint32_t a0, uint32_t b0, int kc, uint32_t idesc0) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int q0 = 0; p + q0 < NP; q0 += 4) {
+            const int nq = min(4, NP - p - q0);
+            const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
+            const uint32_t idesc = idesc0 | ((uint32_t)(nq * OZ_N >> 3) << 17);
+            mma_bf16(tmem + (p + q0) * OZ_N, oz_desc(a0 + p * OZ_CHUNK), oz_desc(b0 + q0 * (OZ_N * OZ_KC * 2)),
+                     idesc, acc);
+        }
 }
 
 // Up to four jobs run as one task list (their targets must not overlap): task t belongs to the
@@ -233,6 +253,7 @@ __device__ inline int task_planes(const OzGemmJob& job, const unsigned char* sa,
 struct OzJobList {
     OzGemmJob job[4];
     long long end[4];
+    long long spin;                // iteration limit of every mbarrier wait
     int n;
     __device__ const OzGemmJob& pick(long long t, long long& local) const {
         int j = 0;
@@ -279,6 +300,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
         if (lane == 0) {
             // producer: stages (task, kc) in order through the ring, stage s = it % OZ_STAGES
             long long it = 0;
+            long long last_it[OZ_STAGES];            // last iteration issued on each stage
+#pragma unroll
+            for (int q = 0; q < OZ_STAGES; ++q) last_it[q] = -1;
             for (long long t = blockIdx.x; t < ntasks && !*(volatile int*)fail; t += gridDim.x) {
                 const unsigned char *sa, *sb;
                 double* C;
@@ -287,13 +311,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 long long lt;
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, C, c0, mult);
-                const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
+                const int np = MIXED ? task_planes(job, sa, sb, c0) : OZ_S;
+                if (MIXED && job.counts) atomicAdd(&job.counts[np == 0 ? 0 : (np == 1 ? 1 : (np == 3 ? 2 : 3))], 1ull);
+                if (MIXED && np == 0) continue;          // skipped: no stages, no MMAs, no drain
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
-                    if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1))) {
+                    if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1), jobs.spin)) {
                         atomicOr(fail, 1);
                         break;
                     }
+                    last_it[s] = it;
                     mbar_expect_tx(&full[s], (uint32_t)np * (OZ_CHUNK + OZ_N * OZ_KC * 2));
                     const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
                     bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, (uint32_t)np * OZ_CHUNK, &full[s]);
@@ -301,6 +328,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                         bulk_g2s(stB + s * OZ_STAGE_B + p * (OZ_N * OZ_KC * 2),
                                  sb + chunk + p * OZ_CHUNK + (c0 >> 3) * 256, OZ_N * OZ_KC * 2, &full[s]);
                 }
+            }
+            if (*(volatile int*)fail) {
+                // a wait ran out somewhere: let the copies already issued land before the CTA
+                // exits (no later phase of a stage was started, so its last phase's parity is
+                // unambiguous)
+#pragma unroll
+                for (int q = 0; q < OZ_STAGES; ++q)
+                    if (last_it[q] >= 0 && !mbar_wait(&full[q], (uint32_t)((last_it[q] / OZ_STAGES) & 1), OZ_DRAIN_LIMIT))
+                        atomicOr(fail, 16);
             }
         }
     } else if (warp == 0) {
@@ -311,7 +347,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             // N = 64 (q1 - q0 + 1) <= 256 into the columns of groups p + q0 .. p + q1: 10 MMAs
             // per stage instead of 28, and A_p is read from shared memory once per MMA.
             const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
-            long long it = 0, nt = 0;
+            long long it = 0, nt = 0, commits = 0;
             for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
                 const unsigned char *sa, *sb;
                 double* Cq;
@@ -320,27 +356,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 long long lt;
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, Cq, cq, mq);
-                const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
-                if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1))) { atomicOr(fail, 4); break; }
+                const int np = MIXED ? task_planes(job, sa, sb, cq) : OZ_S;
+                if (MIXED && np == 0) { --nt; continue; }   // skipped task: not counted in nt
+                if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1), jobs.spin)) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool bad = false;
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
-                    if (!mbar_wait(&full[s], (uint32_t)((it / OZ_STAGES) & 1))) { atomicOr(fail, 2); bad = true; break; }
+                    if (!mbar_wait(&full[s], (uint32_t)((it / OZ_STAGES) & 1), jobs.spin)) { atomicOr(fail, 2); bad = true; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t a0 = smem_u32(stA + s * OZ_STAGE_A), b0 = smem_u32(stB + s * OZ_STAGE_B);
-                    for (int p = 0; p < np; ++p)
-                        for (int q0 = 0; p + q0 < np; q0 += 4) {
-                            const int nq = min(4, np - p - q0);
-                            const uint32_t acc = (kc > 0 || p > 0) ? 1u : 0u;
-                            const uint32_t idesc = idesc0 | ((uint32_t)(nq * OZ_N >> 3) << 17);
-                            mma_bf16(tmem + (p + q0) * OZ_N, oz_desc(a0 + p * OZ_CHUNK),
-                                     oz_desc(b0 + q0 * (OZ_N * OZ_KC * 2)), idesc, acc);
-                        }
+                    if (!MIXED || np == OZ_S) issue_stage<OZ_S>(tmem, a0, b0, kc, idesc0);
+                    else if (np == 3) issue_stage<3>(tmem, a0, b0, kc, idesc0);
+                    else issue_stage<1>(tmem, a0, b0, kc, idesc0);
                     mma_commit(&empty[s]);
                 }
                 mma_commit(tfull);
+                ++commits;
                 if (bad) break;
+            }
+            if (*(volatile int*)fail && commits > 0) {
+                // the last commit tracks every MMA this thread issued: wait for it before the
+                // tensor memory is freed
+                if (!mbar_wait(tfull, (uint32_t)((commits - 1) & 1), OZ_DRAIN_LIMIT)) atomicOr(fail, 32);
             }
         }
     } else {
@@ -357,23 +395,37 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             long long lt;
             const OzGemmJob& job = jobs.pick(t, lt);
             job.task(lt, sa, sb, C, c0, mult);
-            const int np = MIXED ? task_planes(job, sa, sb) : OZ_S;
-            if (!mbar_wait(tfull, (uint32_t)(nt & 1)) || *(volatile int*)fail) { atomicOr(fail, 8); break; }
+            const int np = MIXED ? task_planes(job, sa, sb, c0) : OZ_S;
+            if (MIXED && np == 0) {
+                // skipped: its entries are below the tolerance; an assigning task writes zeros
+                --nt;
+                if (job.assign) {
+                    double* __restrict__ Cz = C + r + (long long)(c0 + chalf) * 128;
+#pragma unroll
+                    for (int h = 0; h < OZ_EPI_COLS; ++h) Cz[(long long)h * 128] = 0.0;
+                }
+                continue;
+            }
+            // one decision per warp: the TMEM loads below are warp-collective
+            const bool ready = mbar_wait(tfull, (uint32_t)(nt & 1), jobs.spin) && !*(volatile int*)fail;
+            if (!__all_sync(0xffffffffu, ready)) { atomicOr(fail, 8); break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             long long fx[OZ_EPI_COLS];
 #pragma unroll
             for (int cb = 0; cb < OZ_EPI_COLS; cb += 8) {
                 uint32_t v[OZ_G][8];
+                // groups this task did not accumulate hold an earlier task's data: they are not
+                // read and count as 0 (np is the same for every thread of the warp)
 #pragma unroll
-                for (int g = 0; g < OZ_G; ++g)
-                    tmem_ld8x(tmem + ((uint32_t)(quarter * 32) << 16) + g * OZ_N + chalf + cb, v[g]);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                // groups this task did not accumulate hold an earlier task's data: count them as 0
-#pragma unroll
-                for (int g = 1; g < OZ_G; ++g)
-                    if (g >= np)
+                for (int g = 0; g < OZ_G; ++g) {
+                    if (g < np) {
+                        tmem_ld8x(tmem + ((uint32_t)(quarter * 32) << 16) + g * OZ_N + chalf + cb, v[g]);
+                    } else {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) v[g][j] = 0u;
+                    }
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     // exact group sums -> fixed point with unit 2^-46 of s_r s_c.  Group g (at
@@ -469,6 +521,7 @@ int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* 
         jl.end[j] = ctas;
     }
     jl.n = njobs;
+    jl.spin = L.spin > 0 ? L.spin : OZ_SPIN_LIMIT;
     if (ctas <= 0) return 0;
     static const int sms = [] {          // initialised once, also when several host threads launch
         int dev = 0, v = 0;

@@ -335,6 +335,8 @@ static inline OzGemmJob with_policy(OzGemmJob j, const MixedPolicy& pol) {
     j.mixed = pol.on;
     j.e_fp64 = pol.e_fp64;
     j.e_fp32 = pol.e_fp32;
+    j.e_skip = pol.e_skip;
+    j.counts = pol.counts;
     return j;
 }
 // W = L_kk^-1 by columns: warp c of the launch solves L w = e_c by forward substitution with the

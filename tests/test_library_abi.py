@@ -67,3 +67,39 @@ def test_host_only_entry_points(lib):
     assert L.fbt_create(ctypes.byref(h), None, 0, None, 0, 10, None, None, 0, None) == 7
     assert L.mle_loglik(None, None, None) == 7
     assert L.fisher_bt_step(None, None, None) == 7
+
+
+def test_noalloc_entry_point_signature_and_argument_checks(lib):
+    """The allocation-free entry point's exports, signatures in the binding, and the argument
+    rejections that happen before any CUDA call (so they run without a GPU)."""
+    from paper_2601_11437_gb300 import _lib
+    L = _lib.load()
+    assert "fbt_noalloc_max_n" in declared_functions() and "fbt_loglik_noalloc" in declared_functions()
+    res, args = _lib.SIGNATURES["fbt_noalloc_max_n"]
+    assert res is ctypes.c_longlong and args == []
+    res, args = _lib.SIGNATURES["fbt_loglik_noalloc"]
+    assert res is ctypes.c_int
+    assert args == [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                    ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                    ctypes.c_void_p]
+    max_n = L.fbt_noalloc_max_n()
+    assert max_n == 1024
+    import numpy as np
+    locs = np.zeros((max_n + 1, 2))
+    z = np.zeros(max_n + 1)
+    th = (ctypes.c_double * 3)(1.0, 0.1, 0.5)
+    out = ctypes.c_double(0.0)
+    pl, pz = locs.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p)
+    ARG, DOMAIN = 7, 1
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 0, th, 1e-8, ctypes.byref(out), None) == ARG          # n < 1
+    assert L.fbt_loglik_noalloc(pl, pz, 0, max_n + 1, th, 1e-8, ctypes.byref(out), None) == ARG  # n > max
+    assert L.fbt_loglik_noalloc(None, pz, 0, 10, th, 1e-8, ctypes.byref(out), None) == ARG        # NULL
+    assert L.fbt_loglik_noalloc(pl, None, 0, 10, th, 1e-8, ctypes.byref(out), None) == ARG
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, None, 1e-8, ctypes.byref(out), None) == ARG
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, th, 1e-8, None, None) == ARG
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, th, -1e-8, ctypes.byref(out), None) == ARG         # jitter < 0
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, th, float("nan"), ctypes.byref(out), None) == ARG
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, th, float("inf"), ctypes.byref(out), None) == ARG
+    bad = (ctypes.c_double * 3)(1.0, 0.0, 0.5)
+    assert L.fbt_loglik_noalloc(pl, pz, 0, 10, bad, 1e-8, ctypes.byref(out), None) == DOMAIN
+    assert out.value == float("-inf")

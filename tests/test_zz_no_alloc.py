@@ -59,6 +59,47 @@ def test_noalloc_matches_mle_loglik_on_two_calls_in_a_row():
         assert ll == pytest.approx(ref, rel=TOL)
 
 
+def test_noalloc_at_the_maximum_size():
+    """n = FBT_NOALLOC_MAX_N: the tile slab nearly fills the scratch array."""
+    require_gpu()
+    import paper_2601_11437_gb300 as fbt
+    lib = fbt._lib.load()
+    n = lib.fbt_noalloc_max_n()
+    locs = inputs.uniform_locations(n, 23)
+    z = fields.sample_field(locs, inputs.standard_normal(n, 23), (1.0, 0.1, 0.8))
+    theta = (0.9, 0.08, 0.7)
+    st, ll = noalloc_loglik(lib, locs, z, theta)
+    assert st == 0, fbt.FbtError(st, "fbt_loglik_noalloc")
+    ctx = fbt.fbt_create(locs, z, nb=64, with_derivatives=False)
+    ref = fbt.mle_loglik(ctx, theta)
+    fbt.fbt_destroy(ctx)
+    assert ll == pytest.approx(ref, rel=TOL)
+
+
+def test_noalloc_call_after_a_failed_call_starts_clean():
+    """A covariance that is not positive definite sets the status word; the next call clears it.
+
+    All points at one location with no jitter give Sigma = sigma^2 * ones (rank one): with
+    sigma^2 = 1 the second pivot of the Cholesky is exactly 0."""
+    require_gpu()
+    import paper_2601_11437_gb300 as fbt
+    lib = fbt._lib.load()
+    n = 50
+    locs = np.tile([[0.25, 0.75]], (n, 1))
+    z = inputs.standard_normal(n, 24)
+    st, ll = noalloc_loglik(lib, locs, z, (1.0, 0.1, 0.5), jitter=0.0)
+    assert st == fbt.FBT_ERR_NOT_PD and ll == -math.inf
+    locs = inputs.uniform_locations(n, 24)
+    z = fields.sample_field(locs, inputs.standard_normal(n, 24), (1.0, 0.1, 0.5))
+    theta = (1.1, 0.09, 0.6)
+    st, ll = noalloc_loglik(lib, locs, z, theta)
+    assert st == 0 and math.isfinite(ll)
+    ctx = fbt.fbt_create(locs, z, nb=64, with_derivatives=False)
+    ref = fbt.mle_loglik(ctx, theta)
+    fbt.fbt_destroy(ctx)
+    assert ll == pytest.approx(ref, rel=TOL)
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum_and_bad_parameters():
     require_gpu()
     import paper_2601_11437_gb300 as fbt
