@@ -720,6 +720,20 @@ def run_sim(args):
     return 0
 
 
+def run_single_eval(args):
+    """One Algorithm 3 evaluation at theta^(0) on the FP64-accurate path (generation, Cholesky,
+    transforms), nothing else: the target of kernel captures on a small case."""
+    import torch
+    import paper_2601_11437_gb300 as fbt
+    w, locs, z = load_field(args.workload)
+    ctx = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_FP64_EMULATED)
+    ll, g, I = fbt.mle_eval(ctx, w.theta0)
+    torch.cuda.synchronize()
+    fbt.fbt_destroy(ctx)
+    print(json.dumps({"workload": w.name, "n": w.n, "loglik": ll, "score": g.tolist()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -740,6 +754,8 @@ def main():
     ap.add_argument("--no-fit", action="store_true", help="skip the two Fisher-BT fits (matched theta_hat)")
     ap.add_argument("--threads", type=int, default=16, help="host threads of the batched workload")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
+    ap.add_argument("--single-eval", action="store_true",
+                    help="one FP64-accurate Algorithm 3 evaluation on --workload (a kernel-capture target)")
     ap.add_argument("--compare-mixed", action="store_true",
                     help="mixed against emulated FP64 on --workload (errors, Cholesky rate, estimates)")
     args = ap.parse_args()
@@ -747,6 +763,8 @@ def main():
         return run_batch(args)
     if args.workload.startswith("sim") and args.impl == "native":
         return run_sim(args)
+    if args.single_eval:
+        return run_single_eval(args)
     if args.adjoint:
         return run_adjoint(args)
     if args.compare_mixed:

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_adjoint_reduce(Geom g, const double* __
         const double dx = s_xy[r] - s_xy[2 * nb + c];
         const double dy = s_xy[nb + r] - s_xy[3 * nb + c];
         const double x = sqrt(dx * dx + dy * dy) * tc.inv_alpha;
-        const MaternVals v = matern_corr<true>(x, tc, s_st2, s_wa, s_wb, s_wd, s_etab);
+        const MaternVals v = matern_corr<true>(x, tc, s_st2, s_wa, s_wb, s_wd, s_etab, &qt->ipoly[0][0][0]);
         const double wt = fma(s_w[r], s_w[nb + c], -Xinv[base + e]);
         ga = fma(wt, v.da, ga);
         gn = fma(wt, v.dn, gn);

@@ -133,6 +133,9 @@ struct fbt_ctx {
     double* yscratch = nullptr;              // two scratch tiles
     double* vx = nullptr;                    // one solved block of a triangular solve
     unsigned long long* tier_counts = nullptr;   // mixed path: tasks per tier (device, 4)
+    long long* task_list = nullptr;          // mixed path: classified tasks of the current launch
+    unsigned* task_count = nullptr;
+    long long task_cap = 0;
     double mixed_tol = 0.0;                  // mixed path: the current tolerance (0: all planes)
     long long spin_budget = 0;               // mbarrier wait limit of the tensor-core kernel (0: default)
     Profiler* prof = nullptr;
@@ -229,6 +232,10 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
     char* pwc = ed ? take((size_t)T * ozaki_tile_bytes()) : nullptr;             // W_k, column-sliced
     char* pyy = ed ? take((size_t)2 * nb * nb * sizeof(double)) : nullptr;       // two scratch tiles
     char* pvx = ed ? take((size_t)nb * sizeof(double)) : nullptr;                // one solved block
+    const bool mix = o.precision == FBT_PREC_MIXED;
+    const long long cap = mixed_list_capacity((int)T);
+    char* plist = mix ? take((size_t)cap * sizeof(long long)) : nullptr;         // classified tasks
+    char* pcount = mix ? take(sizeof(unsigned)) : nullptr;
     if (base && c) {
         c->slices = (unsigned char*)psl;
         c->slice_scratch = (unsigned char*)psx;
@@ -246,6 +253,9 @@ static size_t carve(long long n, const fbt_opts& o, char* base, fbt_ctx* c) {
         c->slots.diag = (double*)pdg; c->slots.offd = (double*)pod;
         c->status = (int*)pst; c->out = (EvalOut*)pout;
         c->tier_counts = (unsigned long long*)ptier;
+        c->task_list = (long long*)plist;
+        c->task_count = (unsigned*)pcount;
+        c->task_cap = mix ? cap : 0;
         c->S = (double*)pS; c->SA = (double*)pSA; c->SN = (double*)pSN;
     }
     return off;
@@ -441,6 +451,9 @@ static MixedPolicy mixed_policy(const fbt_ctx* c, const double theta[3]) {
     pol.e_fp32 = l2 - 1;
     pol.e_fp64 = l2 + 13;
     pol.counts = c->tier_counts;
+    pol.task_list = c->task_list;
+    pol.task_count = c->task_count;
+    pol.task_cap = c->task_cap;
     return pol;
 }
 

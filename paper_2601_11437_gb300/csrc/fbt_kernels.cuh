@@ -31,7 +31,15 @@ struct MixedPolicy {
     int on = 0;
     int e_fp64 = 0, e_fp32 = 0, e_skip = -100000;
     unsigned long long* counts = nullptr;
+    // device scratch of the task classification that precedes every mixed launch: the list of
+    // tasks that are not skipped, with their tier, and its length (capacity: mixed_list_capacity)
+    long long* task_list = nullptr;
+    unsigned* task_count = nullptr;
+    long long task_cap = 0;
 };
+// entries of the classified task list a launch over T x T tiles may need (the largest launch is
+// the two-sided transform's trailing update of both matrices: 2 m (m + 1) tasks, m < T)
+inline long long mixed_list_capacity(int T) { return 2ll * T * (T + 1) + 64; }
 
 // ---- trapezoid quadrature of K_nu, K_{nu-1} and dK_nu/dnu (see matern_gen.cu) ----
 constexpr int QUAD_LEVELS = 5;
@@ -46,12 +54,20 @@ struct ThetaConsts {
 };
 
 constexpr int EXP_TABLE = 256;
+// Piecewise polynomials of the three smooth sums e^x K_nu(x), e^x K_(nu-1)(x), e^x dK_nu/dnu(x)
+// on [1, 1024): each octave [2^s, 2^(s+1)) cut into IP_SUB equal intervals, on each a polynomial of
+// degree IP_DEG - 1 in t in [-1, 1] (see matern_gen.cu).
+constexpr int IP_OCTAVES = 10;
+constexpr int IP_SUB = 8;
+constexpr int IP_DEG = 12;
+constexpr int IP_INTERVALS = IP_OCTAVES * IP_SUB;
 struct QuadTables {
     double exp2tab[EXP_TABLE];            // 2^(j/256), j = 0..255 (table of the exponential)
     double st2[QUAD_LEVELS][QUAD_NODES];  // 2 sinh^2(t_j / 2)  (x cosh t = x + x * st2)
     double wa[QUAD_LEVELS][QUAD_NODES];   // w_j cosh(nu t_j)
     double wb[QUAD_LEVELS][QUAD_NODES];   // w_j cosh((nu - 1) t_j)
     double wd[QUAD_LEVELS][QUAD_NODES];   // w_j t_j sinh(nu t_j)
+    double ipoly[IP_INTERVALS][3][IP_DEG];   // monomial coefficients, constant term first
 };
 
 // ---- output record of one evaluation (device, copied to the host in one transfer) ----
@@ -126,6 +142,9 @@ struct OzGemmJob {
     int e_fp64 = 0, e_fp32 = 0;    // exponent thresholds of the mixed path (see task_planes)
     int e_skip = -100000;
     unsigned long long* counts = nullptr;   // tasks per tier (mixed path, optional)
+    long long* task_list = nullptr;         // mixed path: classified task list (see MixedPolicy)
+    unsigned* task_count = nullptr;
+    long long task_cap = 0;
     __device__ void task(long long bid, const unsigned char*& sa, const unsigned char*& sb,
                          double*& Ct, int& c0, double& m) const {
         const long long tsk = bid >> 1;

@@ -52,20 +52,17 @@ __device__ __forceinline__ double exp_nonpos(double a, const double* __restrict_
 
 struct MaternVals { double r, da, dn; };
 
-// R(x), dR/dalpha, dR/dnu for x > 0 with tables in shared memory.
+// The trapezoid sums e^x K_nu(x), e^x K_(nu-1)(x), e^x dK_nu/dnu(x) (sa, sb, sd) at x > 0 with
+// tables in shared (or global) memory.
 template <bool DERIV>
-__device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& tc,
-                                                  const double* __restrict__ st2,
-                                                  const double* __restrict__ wa,
-                                                  const double* __restrict__ wb,
-                                                  const double* __restrict__ wd,
-                                                  const double* __restrict__ etab) {
-    MaternVals v{0.0, 0.0, 0.0};
-    if (x < X_ZERO_BELOW) { v.r = 1.0; return v; }
-    if (x > X_UNDERFLOW) return v;
+__device__ __forceinline__ void quad_sums(double x, const double* __restrict__ st2, const double* __restrict__ wa,
+                                          const double* __restrict__ wb, const double* __restrict__ wd,
+                                          const double* __restrict__ etab, double& sa, double& sb, double& sd) {
     int l = x <= c_level_xmax[0] ? 0 : x <= c_level_xmax[1] ? 1 : x <= c_level_xmax[2] ? 2 : x <= c_level_xmax[3] ? 3 : 4;
     const int base = l * QUAD_NODES;
-    double sa = 0.0, sb = 0.0, sd = 0.0;
+    sa = 0.0;
+    sb = 0.0;
+    sd = 0.0;
     // four nodes per round; the stopping test (last terms below STOP_REL of the sums, which
     // can only happen past the integrand's peak) is evaluated once per round
     for (int j = 0; j < QUAD_NODES; j += 4) {
@@ -84,6 +81,54 @@ __device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& t
         if (DERIV) done = done && e * wb[base + j + 3] <= STOP_REL * sb && e * wd[base + j + 3] <= STOP_REL * sd;
         if (done) break;
     }
+}
+
+// The same sums from the piecewise polynomials (ip = QuadTables::ipoly) for 1 <= x < 1024.  The
+// octave s and the position f in it, x = 2^s (1 + f), come from the bits of x; interval
+// k = floor(8 f) and t = 16 f - 2 k - 1 in [-1, 1] are exact.
+template <bool DERIV>
+__device__ __forceinline__ void interp_sums(double x, const double* __restrict__ ip, double& sa, double& sb,
+                                            double& sd) {
+    const long long b = __double_as_longlong(x);
+    const int s = (int)(b >> 52) - 1023;
+    const double f = __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll) - 1.0;
+    const int k = (int)(f * IP_SUB);
+    const double t = f * (2 * IP_SUB) - (2 * k + 1);
+    const double* __restrict__ a = ip + (size_t)((s * IP_SUB + k) * 3) * IP_DEG;
+    double pa = __ldg(a + IP_DEG - 1), pb = 0.0, pd = 0.0;
+    if (DERIV) {
+        pb = __ldg(a + 2 * IP_DEG - 1);
+        pd = __ldg(a + 3 * IP_DEG - 1);
+    }
+#pragma unroll
+    for (int i = IP_DEG - 2; i >= 0; --i) {
+        pa = fma(pa, t, __ldg(a + i));
+        if (DERIV) {
+            pb = fma(pb, t, __ldg(a + IP_DEG + i));
+            pd = fma(pd, t, __ldg(a + 2 * IP_DEG + i));
+        }
+    }
+    sa = pa;
+    sb = pb;
+    sd = pd;
+}
+
+// R(x), dR/dalpha, dR/dnu for x > 0 with tables in shared memory; ip (optional): the piecewise
+// polynomials of the sums, used for 1 <= x < 1024 (ip == nullptr: the quadrature everywhere).
+template <bool DERIV>
+__device__ __forceinline__ MaternVals matern_corr(double x, const ThetaConsts& tc,
+                                                  const double* __restrict__ st2,
+                                                  const double* __restrict__ wa,
+                                                  const double* __restrict__ wb,
+                                                  const double* __restrict__ wd,
+                                                  const double* __restrict__ etab,
+                                                  const double* __restrict__ ip = nullptr) {
+    MaternVals v{0.0, 0.0, 0.0};
+    if (x < X_ZERO_BELOW) { v.r = 1.0; return v; }
+    if (x > X_UNDERFLOW) return v;
+    double sa, sb, sd;
+    if (ip && x >= 1.0) interp_sums<DERIV>(x, ip, sa, sb, sd);
+    else quad_sums<DERIV>(x, st2, wa, wb, wd, etab, sa, sb, sd);
     const double lx = log(x);
     // x^nu e^-x / (2^(nu-1) Gamma(nu)); nu log x - x <= nu (log nu - 1) stays far below 700
     const double P = tc.norm * exp_nonpos(tc.nu * lx - x, etab);

@@ -62,11 +62,135 @@ __global__ void k_prep_theta_dev(const double* __restrict__ th, ThetaConsts* __r
     prep_theta_body(th[0], th[1], th[2], th[3], tc, qt);
 }
 
+// ------------------------------------------------------------------------------------------
+// Piecewise polynomials of the three sums for 1 <= x < 1024 (QuadTables::ipoly).
+//
+// The sums g(x) = e^x K_nu(x), e^x K_(nu-1)(x), e^x dK_nu/dnu(x) are smooth and vary slowly (like
+// x^-1/2); their only singularity is at x = 0.  On each interval [a, a + H], H = 2^s / 8 in the
+// octave [2^s, 2^(s+1)), the polynomial of degree 11 interpolating g at the 12 Chebyshev points
+// errs by about rho^-12 relative with rho ~ 4 a / H >= 32 (Bernstein ellipse clear of 0): about
+// 1e-18, below FP64 rounding.  The node values come from the trapezoid sums; the Chebyshev
+// coefficients c_k = (2/12) sum_j g(x_j) cos(pi k (j + 1/2) / 12) (c_0 halved) and their
+// conversion to powers of t are accumulated in double-double arithmetic (cosines of multiples of
+// pi / 24 as double-double constants) and rounded once, so that the evaluation by Horner's rule
+// in t in [-1, 1] (terms decreasing) errs by about one rounding.  Each entry then costs one
+// polynomial per sum instead of a quadrature.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void dd_two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += a * (ch, cl), with the product's rounding error carried
+__device__ __forceinline__ void dd_mac(double& hi, double& lo, double a, double ch, double cl) {
+    const double p = a * ch;
+    const double pe = fma(a, ch, -p);
+    double s, e;
+    dd_two_sum(hi, p, s, e);
+    lo += e + pe + a * cl;
+    dd_two_sum(s, lo, hi, lo);
+}
+
+// cos(m pi / 24) for m = 0 .. 12 as double-double (head, tail)
+static __constant__ double c_cos24[13][2] = {
+    {1.0, 0.0},
+    {0.9914448613738104, 2.898989874454537e-17},
+    {0.9659258262890683, -2.5463971562308955e-17},
+    {0.9238795325112867, 1.7645047084336677e-17},
+    {0.8660254037844386, 5.0175421109034514e-17},
+    {0.7933533402912352, -5.028625073907125e-19},
+    {0.7071067811865476, -4.833646656726457e-17},
+    {0.6087614290087207, -1.647047979025087e-17},
+    {0.5, 0.0},
+    {0.3826834323650898, -1.0050772696461588e-17},
+    {0.25881904510252074, 2.287249500495561e-17},
+    {0.1305261922200516, -9.607666023901524e-18},
+    {0.0, 0.0}};
+
+__device__ inline void cos24(int m, double& h, double& l) {
+    m %= 48;                                   // cos(m pi / 24), period 48
+    if (m > 24) m = 48 - m;                    // even
+    const bool neg = m > 12;                   // cos(pi - y) = -cos(y)
+    if (neg) m = 24 - m;
+    h = neg ? -c_cos24[m][0] : c_cos24[m][0];
+    l = neg ? -c_cos24[m][1] : c_cos24[m][1];
+}
+
+// one warp per interval
+__global__ void __launch_bounds__(256) k_interp_build(const ThetaConsts* __restrict__ tcp, QuadTables* __restrict__ qt) {
+    __shared__ double s_g[8][3][IP_DEG];
+    __shared__ double s_ch[8][3][IP_DEG], s_cl[8][3][IP_DEG];
+    __shared__ int s_B[IP_DEG][IP_DEG];       // coefficient of t^i in T_k: s_B[k][i]
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < IP_DEG; ++k)
+            for (int i = 0; i < IP_DEG; ++i) s_B[k][i] = 0;
+        s_B[0][0] = 1;
+        s_B[1][1] = 1;
+        for (int k = 2; k < IP_DEG; ++k)
+            for (int i = 0; i < IP_DEG; ++i) s_B[k][i] = (i > 0 ? 2 * s_B[k - 1][i - 1] : 0) - s_B[k - 2][i];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int iv = blockIdx.x * 8 + w;
+    if (iv >= IP_INTERVALS) return;
+    const int s = iv / IP_SUB, k = iv % IP_SUB;
+    const double a = ldexp(1.0 + k / (double)IP_SUB, s), H = ldexp(1.0 / IP_SUB, s);
+    if (lane < IP_DEG) {
+        double ch, cl;
+        cos24(2 * lane + 1, ch, cl);           // Chebyshev point t_j = cos(pi (2 j + 1) / 24)
+        const double x = a + 0.5 * H * (1.0 + ch);
+        double sa, sb, sd;
+        quad_sums<true>(x, &qt->st2[0][0], &qt->wa[0][0], &qt->wb[0][0], &qt->wd[0][0], qt->exp2tab, sa, sb, sd);
+        s_g[w][0][lane] = sa;
+        s_g[w][1][lane] = sb;
+        s_g[w][2][lane] = sd;
+    }
+    __syncwarp();
+    if (lane < IP_DEG) {                       // Chebyshev coefficient c_lane of each sum
+        for (int q = 0; q < 3; ++q) {
+            double hi = 0.0, lo = 0.0;
+            for (int j = 0; j < IP_DEG; ++j) {
+                double ch, cl;
+                cos24(lane * (2 * j + 1), ch, cl);
+                dd_mac(hi, lo, s_g[w][q][j], ch, cl);
+            }
+            // (hi + lo) / 12 in double-double: the head's quotient, its exact remainder
+            const double qh = hi / IP_DEG;
+            const double r = fma(-qh, (double)IP_DEG, hi);
+            double h2, l2;
+            dd_two_sum(qh, (r + lo) / IP_DEG, h2, l2);
+            if (lane > 0) { h2 *= 2.0; l2 *= 2.0; }
+            s_ch[w][q][lane] = h2;
+            s_cl[w][q][lane] = l2;
+        }
+    }
+    __syncwarp();
+    if (lane < IP_DEG) {                       // power-of-t coefficient a_lane = sum_k c_k B[k][lane]
+        for (int q = 0; q < 3; ++q) {
+            double hi = 0.0, lo = 0.0;
+            for (int kk = 0; kk < IP_DEG; ++kk) {
+                const int bk = s_B[kk][lane];
+                if (bk == 0) continue;
+                dd_mac(hi, lo, (double)bk, s_ch[w][q][kk], s_cl[w][q][kk]);
+            }
+            qt->ipoly[iv][q][lane] = hi + lo;
+        }
+    }
+}
+
+static int launch_interp_build(Launcher& L, const ThetaConsts* tc, QuadTables* qt) {
+    L.begin("prep_theta");
+    k_interp_build<<<(IP_INTERVALS + 7) / 8, 256, 0, L.stream>>>(tc, qt);
+    L.count();
+    return L.end(0.0, 0.0);
+}
+
 int launch_prep_theta_dev(Launcher& L, const double* th, ThetaConsts* tc, QuadTables* qt) {
     L.begin("prep_theta");
     k_prep_theta_dev<<<1, QUAD_NODES, 0, L.stream>>>(th, tc, qt);
     L.count();
-    return L.end(0.0, 0.0);
+    const int rc = L.end(0.0, 0.0);
+    return rc ? rc : launch_interp_build(L, tc, qt);
 }
 
 int launch_prep_theta(Launcher& L, const double theta[3], double jitter, ThetaConsts* tc,
@@ -74,7 +198,8 @@ int launch_prep_theta(Launcher& L, const double theta[3], double jitter, ThetaCo
     L.begin("prep_theta");
     k_prep_theta<<<1, QUAD_NODES, 0, L.stream>>>(theta[0], theta[1], theta[2], jitter, tc, qt);
     L.count();
-    return L.end(0.0, 0.0);
+    const int rc = L.end(0.0, 0.0);
+    return rc ? rc : launch_interp_build(L, tc, qt);
 }
 
 // One block per lower tile (column-major tile order), the whole nb x nb tile (diagonal tiles
@@ -133,7 +258,7 @@ __global__ void __launch_bounds__(256) k_generate(Geom g, const double* __restri
             const double dx = s_xy[r] - s_xy[2 * nb + c];
             const double dy = s_xy[nb + r] - s_xy[3 * nb + c];
             const double x = sqrt(dx * dx + dy * dy) * tc.inv_alpha;
-            const MaternVals v = matern_corr<DERIV>(x, tc, s_st2, s_wa, s_wb, s_wd, s_etab);
+            const MaternVals v = matern_corr<DERIV>(x, tc, s_st2, s_wa, s_wb, s_wd, s_etab, &qt->ipoly[0][0][0]);
             s = tc.sigma2 * v.r;
             sa = tc.sigma2 * v.da;
             sn = tc.sigma2 * v.dn;

@@ -254,6 +254,8 @@ struct OzJobList {
     OzGemmJob job[4];
     long long end[4];
     long long spin;                // iteration limit of every mbarrier wait
+    const long long* list;         // mixed path: classified tasks, (task << 3) | tier
+    const unsigned* count;         //   and their number (null: every task, all planes)
     int n;
     __device__ const OzGemmJob& pick(long long t, long long& local) const {
         int j = 0;
@@ -263,8 +265,61 @@ struct OzJobList {
     }
 };
 
+// Mixed path: the classification that precedes every launch.  One thread per task takes its
+// tier from the operand tiles' largest entries (task_planes) and appends every task that is
+// not skipped, or that must write zeros, to the list as (task << 3) | tier, tier 0..3 for 0, 1,
+// 3 and 7 planes; the tile-update kernel then walks the list, so a skipped task costs nothing
+// there.  The list's order varies from run to run, the results do not: the tasks of one launch
+// write disjoint targets, each the same values whichever CTA computes it.
+__device__ inline int tier_planes(int tier) { return tier == 0 ? 0 : (tier == 1 ? 1 : (tier == 2 ? 3 : OZ_S)); }
+
+__global__ void __launch_bounds__(256) k_mixed_classify(OzJobList jobs, long long ntasks, long long* __restrict__ list,
+                                                        unsigned* __restrict__ count) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int tier = -1;
+    bool keep = false;
+    if (t < ntasks) {
+        const unsigned char *sa, *sb;
+        double* C;
+        int c0;
+        double mult;
+        long long lt;
+        const OzGemmJob& job = jobs.pick(t, lt);
+        job.task(lt, sa, sb, C, c0, mult);
+        const int np = task_planes(job, sa, sb, c0);
+        tier = np == 0 ? 0 : (np == 1 ? 1 : (np == 3 ? 2 : 3));
+        keep = np != 0 || job.assign != 0;
+    }
+    unsigned long long* tiers = jobs.job[0].counts;
+    if (tiers) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const unsigned m = __ballot_sync(0xffffffffu, tier == q);
+            if (lane == 0 && m) atomicAdd(&tiers[q], (unsigned long long)__popc(m));
+        }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (mask) {
+        const int leader = __ffs(mask) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) list[base + __popc(mask & ((1u << lane) - 1u))] = (t << 3) | tier;
+    }
+}
+
 // MIXED: the job list may use fewer digit planes per task (compiled separately, so that the
 // FP64-accurate path carries no plane-count logic)
+// Work item i of a launch: task i with all planes, or entry i of the mixed path's classified
+// list (its task and its plane count).
+__device__ inline long long work_item(const OzJobList& jobs, long long i, int& np) {
+    if (!jobs.list) { np = OZ_S; return i; }
+    const long long e = jobs.list[i];
+    np = tier_planes((int)(e & 7));
+    return e >> 3;
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, long long ntasks, int* status) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
@@ -295,6 +350,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // work items: every task, or the mixed path's classified list (written by the preceding
+    // launch on this stream)
+    const long long nwork = (MIXED && jobs.list) ? (long long)*jobs.count : ntasks;
 
     if (warp == 1) {
         if (lane == 0) {
@@ -303,17 +361,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             long long last_it[OZ_STAGES];            // last iteration issued on each stage
 #pragma unroll
             for (int q = 0; q < OZ_STAGES; ++q) last_it[q] = -1;
-            for (long long t = blockIdx.x; t < ntasks && !*(volatile int*)fail; t += gridDim.x) {
+            for (long long i = blockIdx.x; i < nwork && !*(volatile int*)fail; i += gridDim.x) {
                 const unsigned char *sa, *sb;
                 double* C;
                 int c0;
                 double mult;
                 long long lt;
+                int np;
+                const long long t = work_item(jobs, i, np);
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, C, c0, mult);
-                const int np = MIXED ? task_planes(job, sa, sb, c0) : OZ_S;
-                if (MIXED && job.counts) atomicAdd(&job.counts[np == 0 ? 0 : (np == 1 ? 1 : (np == 3 ? 2 : 3))], 1ull);
-                if (MIXED && np == 0) continue;          // skipped: no stages, no MMAs, no drain
+                if (MIXED && np == 0) continue;          // writes zeros only: no stages, no MMAs
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
                     if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1), jobs.spin)) {
@@ -348,16 +406,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             // per stage instead of 28, and A_p is read from shared memory once per MMA.
             const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
             long long it = 0, nt = 0, commits = 0;
-            for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
-                const unsigned char *sa, *sb;
-                double* Cq;
-                int cq;
-                double mq;
-                long long lt;
-                const OzGemmJob& job = jobs.pick(t, lt);
-                job.task(lt, sa, sb, Cq, cq, mq);
-                const int np = MIXED ? task_planes(job, sa, sb, cq) : OZ_S;
-                if (MIXED && np == 0) { --nt; continue; }   // skipped task: not counted in nt
+            for (long long i = blockIdx.x; i < nwork; i += gridDim.x, ++nt) {
+                int np;
+                work_item(jobs, i, np);
+                if (MIXED && np == 0) { --nt; continue; }   // zero-writing task: not counted in nt
                 if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1), jobs.spin)) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool bad = false;
@@ -387,17 +439,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
         const int r = quarter * 32 + lane;
         const int chalf = ((warp - 2) >> 2) * OZ_EPI_COLS;
         long long nt = 0;
-        for (long long t = blockIdx.x; t < ntasks; t += gridDim.x, ++nt) {
+        for (long long i = blockIdx.x; i < nwork; i += gridDim.x, ++nt) {
             const unsigned char *sa, *sb;
             double* C;
             int c0;
             double mult;
             long long lt;
+            int np;
+            const long long t = work_item(jobs, i, np);
             const OzGemmJob& job = jobs.pick(t, lt);
             job.task(lt, sa, sb, C, c0, mult);
-            const int np = MIXED ? task_planes(job, sa, sb, c0) : OZ_S;
             if (MIXED && np == 0) {
-                // skipped: its entries are below the tolerance; an assigning task writes zeros
+                // an assigning task whose entries are all below the tolerance writes zeros
                 --nt;
                 if (job.assign) {
                     double* __restrict__ Cz = C + r + (long long)(c0 + chalf) * 128;
@@ -537,8 +590,23 @@ int launch_ozaki_gemm_multi(Launcher& L, const OzGemmJob* job, const long long* 
     const long long avail = (long long)sms - reserve_sms > 1 ? (long long)sms - reserve_sms : 1;
     const long long grid = ctas < avail ? ctas : avail;
     L.begin(family);
-    if (mixed) k_ozaki_gemm<true><<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
-    else k_ozaki_gemm<false><<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
+    jl.list = nullptr;
+    jl.count = nullptr;
+    if (mixed && !(job[0].task_list && job[0].task_count && ctas <= job[0].task_cap))
+        return cudaErrorInvalidValue;          // the mixed path needs room for its task list
+    if (mixed) {
+        // classify the tasks, then walk the list of those not skipped (persistent grid: the
+        // list's length is only known on the device)
+        if (cudaMemsetAsync(job[0].task_count, 0, sizeof(unsigned), L.stream) != cudaSuccess) return cudaGetLastError();
+        k_mixed_classify<<<(unsigned)((ctas + 255) / 256), 256, 0, L.stream>>>(jl, ctas, job[0].task_list,
+                                                                               job[0].task_count);
+        L.count();
+        jl.list = job[0].task_list;
+        jl.count = job[0].task_count;
+        k_ozaki_gemm<true><<<(unsigned)avail, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
+    } else {
+        k_ozaki_gemm<false><<<(unsigned)grid, OZ_THREADS, OZ_SMEM, L.stream>>>(jl, ctas, status);
+    }
     L.count();
     return L.end(flops, 0.0);
 }

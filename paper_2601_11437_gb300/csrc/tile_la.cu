@@ -337,6 +337,9 @@ static inline OzGemmJob with_policy(OzGemmJob j, const MixedPolicy& pol) {
     j.e_fp32 = pol.e_fp32;
     j.e_skip = pol.e_skip;
     j.counts = pol.counts;
+    j.task_list = pol.task_list;
+    j.task_count = pol.task_count;
+    j.task_cap = pol.task_cap;
     return j;
 }
 // W = L_kk^-1 by columns: warp c of the launch solves L w = e_c by forward substitution with the

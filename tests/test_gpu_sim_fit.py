@@ -46,13 +46,16 @@ def test_simulation_field_fit_matches_oracle_algorithm1(path):
         logliks.append(st.loglik)
     assert len(points) == len(rec["fisher_points"])
     np.testing.assert_allclose(np.array(points), np.array(rec["fisher_points"]), rtol=1e-7)
-    np.testing.assert_allclose(np.array(logliks), np.array(rec["fisher_logliks"]), rtol=1e-10)
+    # l is a sum of terms of size O(n) (-n/2 log 2 pi, -1/2 log det, -1/2 z^T Sigma^-1 z) that
+    # nearly cancel along this trajectory: 1e-10 of those terms, not of l itself
+    n = len(z)
+    np.testing.assert_allclose(np.array(logliks), np.array(rec["fisher_logliks"]), rtol=1e-10, atol=1e-10 * n)
     # the whole run (the same start), Nelder-Mead included where the oracle shifts
     fin = fbt.fisher_bt_run(ctx, theta_lo=lo, theta_hi=hi)
     assert fin.state == rec["state"]
     assert (fin.iter, fin.n_ll, fin.n_grad) == (rec["iter"], rec["n_ll"], rec["n_grad"])
     np.testing.assert_allclose(np.array(fin.theta[:]), rec["theta_hat"], rtol=1e-6)
-    assert fin.loglik == pytest.approx(rec["loglik"], rel=1e-10)
+    assert fin.loglik == pytest.approx(rec["loglik"], rel=1e-10, abs=1e-10 * n)
     I, Iref = np.array(fin.fisher[:]).reshape(3, 3), np.array(rec["fisher"]).reshape(3, 3)
     d = np.sqrt(np.diag(Iref))
     assert np.all(np.abs(I - Iref) <= 1e-6 * np.outer(d, d))
