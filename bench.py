@@ -39,6 +39,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the batched modes drive up to 64 streams at once; the runtime maps streams onto this many
+# hardware queues (default 8) when the CUDA context is created
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_2601_11437_gb300 import inputs  # noqa: E402
 
@@ -48,10 +51,10 @@ PRECISIONS = {"fp64": 0, "fp64_emulated": 1, "mixed": 2}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
-# launch of the two-sided transform's trailing update at n = 4096 (read + written bytes over the
-# launch's tasks); the C tiles, which dominate it, grow in proportion to the tasks.  None until a
-# capture of the current kernel exists.
-OZAKI_DRAM_BYTES_PER_TASK = None
+# launch of the two-sided transform's trailing update at n = 4096 (153.246 MB read + 71.072 MB
+# written over the launch's 1984 tasks); the C tiles, which dominate it, grow in proportion to
+# the tasks
+OZAKI_DRAM_BYTES_PER_TASK = (153.246208e6 + 71.072e6) / 1984
 OZAKI_TASK_FLOPS = 2.0 * 128 * 64 * 128
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
@@ -490,8 +493,29 @@ def run_batch(args):
     mine = sharding.partition([f.n ** 3 for f, _, _ in full], world)[rank]
     batch = [full[i] for i in mine]
     prec = PRECISIONS[args.precision]
-    ctxs = [fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=prec) for _, locs, z in batch]
     theta0s = np.array([f.theta0 for f, _, _ in batch])
+    tuning = None
+    if args.autotune and args.precision in ("fp64", "fp64_emulated"):
+        # per size band (n rounded up to a power of two) the faster FP64-accurate configuration,
+        # measured on the band's first field; then the host-thread count over the whole batch
+        choice, bands = {}, {}
+        for f, locs, z in batch:
+            band = 1 << (f.n - 1).bit_length()
+            if band not in choice:
+                p_, nb_, secs, _ = fbt.fbt_autotune(locs, z, f.theta0, precision=prec, device=local)
+                choice[band] = (p_, nb_)
+                bands[str(band)] = {"precision": {v: k for k, v in PRECISIONS.items()}[p_], "nb": nb_,
+                                    "seconds_per_eval": secs}
+        ctxs = []
+        for f, locs, z in batch:
+            p_, nb_ = choice[1 << (f.n - 1).bit_length()]
+            ctxs.append(fbt.fbt_create(locs, z, nb=nb_, device=local, precision=p_))
+        best, secs = fbt.fbt_tune_batch_threads(ctxs, theta0s, candidates=(8, 16, 32, 64))
+        args.threads = best
+        tuning = {"bands": bands, "threads": best, "threads_seconds_per_pass": secs,
+                  "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")}
+    else:
+        ctxs = [fbt.fbt_create(locs, z, nb=args.nb, device=local, precision=prec) for _, locs, z in batch]
     st0, status = fbt.fisher_bt_start_batch(ctxs, theta0s, nthreads=args.threads)
     running = [q for q in range(len(ctxs)) if st0[q].state == fbt.RUNNING]
     run_ctxs = [ctxs[q] for q in running]
@@ -552,7 +576,7 @@ def run_batch(args):
                    "parallelism": f"fields sharded over {world} rank(s) by n^3, records gathered",
                    "n_range": [min(f.n for f, _, _ in full), max(f.n for f, _, _ in full)],
                    "sum_n3": float(sum(float(f.n) ** 3 for f, _, _ in full)),
-                   "precision": args.precision, "threads": args.threads, "nb": args.nb,
+                   "precision": args.precision, "threads": args.threads, "nb": args.nb, "autotune": tuning,
                    "timing": "host wall clock around each batched call (it synchronises every stream)"},
         "aggregate_tflops_fp64_equivalent": flops / sec / 1e12,
         "gpu_launches": launches, "clocks": ck, "e2e": None, "cpu_baseline": None,
@@ -748,11 +772,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-sizes", type=lambda v: [int(x) for x in v.split(",")],
                     default=list(ORACLE_SIZES), help="oracle subsample sizes of the reference arm")
-    ap.add_argument("--mixed-tol", type=float, default=1e-8, help="tolerance of the mixed path's line entry")
+    ap.add_argument("--mixed-tol", type=float, default=1e-6,
+                    help="tolerance of the mixed path's line entry (1e-6: the loosest whose estimate at the "
+                         "switch meets the 1e-3 criterion at n = 65,536)")
     ap.add_argument("--mixed-steps", type=int, default=5, help="timed steps of the mixed path (at most --steps)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-fit", action="store_true", help="skip the two Fisher-BT fits (matched theta_hat)")
     ap.add_argument("--threads", type=int, default=16, help="host threads of the batched workload")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched workload: tune the FP64-accurate configuration per size band and the thread count")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
     ap.add_argument("--single-eval", action="store_true",
                     help="one FP64-accurate Algorithm 3 evaluation on --workload (a kernel-capture target)")

@@ -212,6 +212,30 @@ fbt_status fisher_bt_run_batch(fbt_ctx* const* ctxs, int nfields, const double* 
                                fbt_state* states, int* status, int nthreads);
 
 /*
+ * Autotuners (not in the paper; they choose how the work is run, never what it computes).
+ *
+ * fbt_tune_batch_threads: times one batched Algorithm 2 pass (mle_eval_batch, l only) over the
+ * given fields (thetas: 3 per field) for each candidate host-thread count, after two untimed
+ * passes (direct launches, then graph capture), and returns the fastest count in *best and
+ * each candidate's wall-clock seconds in seconds[ncand].  Many concurrent streams only overlap
+ * on the GPU when the process allows enough hardware queues (CUDA_DEVICE_MAX_CONNECTIONS, an
+ * environment variable read when the CUDA context is created; the default is 8).
+ *
+ * fbt_autotune: for a field of n locations (host arrays, as fbt_create), chooses the faster of
+ * the two FP64-accurate configurations, FBT_PREC_FP64 with nb = 64 (FP64 DFMA tiles) and
+ * FBT_PREC_FP64_EMULATED with nb = 128 (tensor-core tiles), by timing `reps` Algorithm 3
+ * evaluations of each at theta on temporary contexts (after two untimed ones).  opts->precision
+ * must be one of the two; on return opts->precision and opts->nb hold the choice and
+ * seconds[2] the mean seconds per evaluation of (FP64 nb 64, emulated nb 128).  The choice is
+ * cached per device and size band (n rounded up to a power of two): a later call in the band
+ * returns it without measuring (*cached = 1; cached may be NULL).
+ */
+fbt_status fbt_tune_batch_threads(fbt_ctx* const* ctxs, int nfields, const double* thetas, const int* candidates,
+                                  int ncand, int* best, double* seconds);
+fbt_status fbt_autotune(const double* locs, const double* z, long long n, const double theta[3], int reps,
+                        fbt_opts* opts, double seconds[2], int* cached);
+
+/*
  * Graph replay of evaluations (default on).  The launch sequence of an evaluation depends only on
  * its kind (Algorithm 2 with or without kept partials; Algorithm 3 fresh, reusing the factor,
  * or reusing factor and partials), not on theta, which reaches the device through a buffer the

@@ -288,6 +288,35 @@ def fisher_bt_run_batch(ctxs, theta0s=None, theta_lo=None, theta_hi=None, bt=Non
     return states, status
 
 
+def fbt_tune_batch_threads(ctxs, thetas, candidates=(8, 16, 32, 64)):
+    """Autotuner: the fastest host-thread count of the batched entry points on these fields;
+    returns (best, {candidate: seconds})."""
+    F = len(ctxs)
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(F, 3))
+    cand = (C.c_int * len(candidates))(*candidates)
+    secs = (C.c_double * len(candidates))()
+    best = C.c_int()
+    _check(_lib.load().fbt_tune_batch_threads(_handles(ctxs), F, th.ctypes.data_as(_lib.c_double_p), cand,
+                                              len(candidates), C.byref(best), secs), "fbt_tune_batch_threads")
+    return best.value, {c: secs[i] for i, c in enumerate(candidates)}
+
+
+def fbt_autotune(locs, z, theta, *, precision: int = PREC_FP64_EMULATED, reps: int = 2, device: int = 0):
+    """Autotuner: the faster FP64-accurate configuration (precision, nb) for a field of this size;
+    returns (precision, nb, {"fp64_nb64": s, "emulated_nb128": s}, cached)."""
+    lib = _lib.load()
+    opts = FbtOpts()
+    lib.fbt_default_opts(C.byref(opts))
+    opts.precision, opts.device = int(precision), device
+    locs = np.ascontiguousarray(locs, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    secs = (C.c_double * 2)()
+    cached = C.c_int()
+    _check(lib.fbt_autotune(locs.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p), len(z), _dbl3(theta),
+                            int(reps), C.byref(opts), secs, C.byref(cached)), "fbt_autotune")
+    return opts.precision, opts.nb, {"fp64_nb64": secs[0], "emulated_nb128": secs[1]}, bool(cached.value)
+
+
 def fbt_destroy(ctx: Context) -> None:
     if ctx.handle and ctx.handle.value:
         _lib.load().fbt_destroy(ctx.handle)

@@ -59,6 +59,10 @@ SIGNATURES = {
                                        C.POINTER(FbtBtOpts), C.POINTER(C.c_int), C.c_int]),
     "fisher_bt_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, c_double_p, c_double_p,
                                       C.POINTER(FbtBtOpts), C.POINTER(FbtState), C.POINTER(C.c_int), C.c_int]),
+    "fbt_tune_batch_threads": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, c_double_p, C.POINTER(C.c_int), C.c_int,
+                                         C.POINTER(C.c_int), c_double_p]),
+    "fbt_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, c_double_p, C.c_int, C.POINTER(FbtOpts),
+                               c_double_p, C.POINTER(C.c_int)]),
     "fbt_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "fbt_graph_count": (C.c_int, [C.c_void_p]),
     "fbt_set_mixed_tol": (C.c_int, [C.c_void_p, C.c_double]),

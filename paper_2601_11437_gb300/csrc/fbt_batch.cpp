@@ -3,8 +3,13 @@
 // steps of small fields (diagonal factorisations, strip solves, TRSV) of different fields overlap
 // on the GPU while the tile updates of large ones fill it.  Fields are taken largest first
 // (longest-processing-time order); nothing is exchanged between fields.
+#include <math.h>
+
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -145,6 +150,97 @@ fbt_status fisher_bt_run_batch(fbt_ctx* const* ctxs, int nfields, const double* 
         status[f] = (int)s;
         return s;
     });
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuning.  The choices are measured, not modelled: each candidate runs the same work on the
+// caller's data and the fastest wins.
+// ------------------------------------------------------------------------------------------
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+fbt_status fbt_tune_batch_threads(fbt_ctx* const* ctxs, int nfields, const double* thetas, const int* candidates,
+                                  int ncand, int* best, double* seconds) {
+    if (!ctxs || nfields < 1 || !thetas || !candidates || ncand < 1 || !best || !seconds) return FBT_ERR_ARG;
+    for (int i = 0; i < ncand; ++i)
+        if (candidates[i] < 1) return FBT_ERR_ARG;
+    std::vector<double> out(nfields);
+    std::vector<int> st(nfields);
+    // two untimed passes: the first runs each context's launch sequence directly, the second
+    // captures it as a graph, later ones replay it (as every timed pass does)
+    for (int w = 0; w < 2; ++w) {
+        fbt_status s = mle_eval_batch(ctxs, nfields, thetas, 1, FBT_BATCH_LOGLIK, out.data(), st.data(), candidates[0]);
+        if (hard_error(s)) return s;
+    }
+    int arg = 0;
+    for (int i = 0; i < ncand; ++i) {
+        const auto t0 = std::chrono::steady_clock::now();
+        fbt_status s = mle_eval_batch(ctxs, nfields, thetas, 1, FBT_BATCH_LOGLIK, out.data(), st.data(), candidates[i]);
+        seconds[i] = seconds_since(t0);           // the batched call returns with every stream idle
+        if (hard_error(s)) return s;
+        if (seconds[i] < seconds[arg]) arg = i;
+    }
+    *best = candidates[arg];
+    return FBT_OK;
+}
+
+namespace {
+struct TuneRecord {
+    int precision, nb;
+    double seconds[2];
+};
+std::mutex g_tune_mutex;
+std::map<std::pair<int, long long>, TuneRecord> g_tune_cache;     // (device, size band) -> choice
+}  // namespace
+
+fbt_status fbt_autotune(const double* locs, const double* z, long long n, const double theta[3], int reps,
+                        fbt_opts* opts, double seconds[2], int* cached) {
+    if (!locs || !z || n < 1 || !theta || !opts || !seconds || reps < 1) return FBT_ERR_ARG;
+    if (opts->precision != FBT_PREC_FP64 && opts->precision != FBT_PREC_FP64_EMULATED) return FBT_ERR_ARG;
+    long long band = 1;
+    while (band < n) band <<= 1;
+    const std::pair<int, long long> key{opts->device, band};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            opts->precision = it->second.precision;
+            opts->nb = it->second.nb;
+            seconds[0] = it->second.seconds[0];
+            seconds[1] = it->second.seconds[1];
+            if (cached) *cached = 1;
+            return FBT_OK;
+        }
+    }
+    // the two FP64-accurate configurations: FP64 DFMA tiles of 64, tensor-core tiles of 128
+    const int prec[2] = {FBT_PREC_FP64, FBT_PREC_FP64_EMULATED};
+    const int nbs[2] = {64, 128};
+    for (int c = 0; c < 2; ++c) {
+        fbt_opts o = *opts;
+        o.precision = prec[c];
+        o.nb = nbs[c];
+        fbt_ctx* ctx = nullptr;
+        fbt_status s = fbt_create(&ctx, locs, 0, z, 0, n, &o, nullptr, 0, nullptr);
+        if (s != FBT_OK) return s;
+        double ll, g[3], I[9];
+        s = mle_eval(ctx, theta, &ll, g, I);          // untimed: direct launches
+        if (hard_error(s)) { fbt_destroy(ctx); return s; }
+        s = mle_eval(ctx, theta, &ll, g, I);          // untimed: captures the graph
+        if (hard_error(s)) { fbt_destroy(ctx); return s; }
+        const auto t0 = std::chrono::steady_clock::now();
+        for (int r = 0; r < reps && !hard_error(s); ++r) s = mle_eval(ctx, theta, &ll, g, I);
+        seconds[c] = seconds_since(t0) / reps;        // each evaluation synchronises
+        fbt_destroy(ctx);
+        if (hard_error(s)) return s;
+    }
+    const int arg = seconds[1] <= seconds[0] ? 1 : 0;
+    opts->precision = prec[arg];
+    opts->nb = nbs[arg];
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = TuneRecord{prec[arg], nbs[arg], {seconds[0], seconds[1]}};
+    if (cached) *cached = 0;
+    return FBT_OK;
 }
 
 }  // extern "C"

@@ -312,9 +312,10 @@ __global__ void __launch_bounds__(256) k_mixed_classify(OzJobList jobs, long lon
 // MIXED: the job list may use fewer digit planes per task (compiled separately, so that the
 // FP64-accurate path carries no plane-count logic)
 // Work item i of a launch: task i with all planes, or entry i of the mixed path's classified
-// list (its task and its plane count).
+// list (its task and its plane count).  Without MIXED the plane count is a compile-time constant.
+template <bool MIXED>
 __device__ inline long long work_item(const OzJobList& jobs, long long i, int& np) {
-    if (!jobs.list) { np = OZ_S; return i; }
+    if (!MIXED || !jobs.list) { np = OZ_S; return i; }
     const long long e = jobs.list[i];
     np = tier_planes((int)(e & 7));
     return e >> 3;
@@ -357,10 +358,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
     if (warp == 1) {
         if (lane == 0) {
             // producer: stages (task, kc) in order through the ring, stage s = it % OZ_STAGES
-            long long it = 0;
-            long long last_it[OZ_STAGES];            // last iteration issued on each stage
-#pragma unroll
-            for (int q = 0; q < OZ_STAGES; ++q) last_it[q] = -1;
+            long long it = 0;                        // stage iterations issued so far
             for (long long i = blockIdx.x; i < nwork && !*(volatile int*)fail; i += gridDim.x) {
                 const unsigned char *sa, *sb;
                 double* C;
@@ -368,17 +366,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 double mult;
                 long long lt;
                 int np;
-                const long long t = work_item(jobs, i, np);
+                const long long t = work_item<MIXED>(jobs, i, np);
                 const OzGemmJob& job = jobs.pick(t, lt);
                 job.task(lt, sa, sb, C, c0, mult);
                 if (MIXED && np == 0) continue;          // writes zeros only: no stages, no MMAs
+                // the task's 64 columns of C (64 KB, contiguous in the column-major tile) into
+                // L2 now, so that the epilogue's loads of them, a task later, do not wait on DRAM
+                if (!job.assign)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(C + (size_t)c0 * 128),
+                                 "r"(128u * 64u * 8u) : "memory");
                 for (int kc = 0; kc < OZ_NKC; ++kc, ++it) {
                     const int s = (int)(it % OZ_STAGES);
                     if (it >= OZ_STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / OZ_STAGES) - 1) & 1), jobs.spin)) {
                         atomicOr(fail, 1);
                         break;
                     }
-                    last_it[s] = it;
                     mbar_expect_tx(&full[s], (uint32_t)np * (OZ_CHUNK + OZ_N * OZ_KC * 2));
                     const size_t chunk = (size_t)kc * OZ_S * OZ_CHUNK;
                     bulk_g2s(stA + s * OZ_STAGE_A, sa + chunk, (uint32_t)np * OZ_CHUNK, &full[s]);
@@ -389,12 +391,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             }
             if (*(volatile int*)fail) {
                 // a wait ran out somewhere: let the copies already issued land before the CTA
-                // exits (no later phase of a stage was started, so its last phase's parity is
-                // unambiguous)
+                // exits.  Stages are issued round robin, so the last iteration issued on stage q
+                // is it - 1 - ((it - 1 - q) mod OZ_STAGES); no later phase of it was started, so
+                // that phase's parity is unambiguous.
 #pragma unroll
-                for (int q = 0; q < OZ_STAGES; ++q)
-                    if (last_it[q] >= 0 && !mbar_wait(&full[q], (uint32_t)((last_it[q] / OZ_STAGES) & 1), OZ_DRAIN_LIMIT))
-                        atomicOr(fail, 16);
+                for (int q = 0; q < OZ_STAGES; ++q) {
+                    if (it <= q) continue;
+                    const long long last = it - 1 - ((it - 1 - q) % OZ_STAGES);
+                    if (!mbar_wait(&full[q], (uint32_t)((last / OZ_STAGES) & 1), OZ_DRAIN_LIMIT)) atomicOr(fail, 16);
+                }
             }
         }
     } else if (warp == 0) {
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             long long it = 0, nt = 0, commits = 0;
             for (long long i = blockIdx.x; i < nwork; i += gridDim.x, ++nt) {
                 int np;
-                work_item(jobs, i, np);
+                work_item<MIXED>(jobs, i, np);
                 if (MIXED && np == 0) { --nt; continue; }   // zero-writing task: not counted in nt
                 if (nt > 0 && !mbar_wait(tempty, (uint32_t)((nt - 1) & 1), jobs.spin)) { atomicOr(fail, 4); break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
             double mult;
             long long lt;
             int np;
-            const long long t = work_item(jobs, i, np);
+            const long long t = work_item<MIXED>(jobs, i, np);
             const OzGemmJob& job = jobs.pick(t, lt);
             job.task(lt, sa, sb, C, c0, mult);
             if (MIXED && np == 0) {
