@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["reorder.cu", "matern_gen.cu", "tile_la.cu", "vec_la.cu", "fbt_api.cu", "fisher_bt.cpp",
            "fbt_noalloc.cu", "ozaki.cu", "adjoint.cu", "fbt_batch.cpp"]
-HEADERS = [os.path.join(CSRC, h) for h in ("fbt_kernels.cuh", "fbt_matern.cuh", "fbt_ctx_access.h")] + \
+HEADERS = [os.path.join(CSRC, h) for h in ("fbt_kernels.cuh", "fbt_matern.cuh", "fbt_ctx_access.h", "fbt_fx.h")] + \
           [os.path.join(INCLUDE, "fbt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I", INCLUDE]

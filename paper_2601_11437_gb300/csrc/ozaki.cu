@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include "fbt_kernels.cuh"
+#include "fbt_fx.h"
 
 namespace fbt {
 
@@ -198,23 +199,15 @@ __device__ inline void tmem_ld8x(uint32_t taddr, uint32_t r[8]) {
                  : "r"(taddr));
 }
 
-// (double)fx * 2^s, with the power of two applied by exponent arithmetic when the result stays
-// normal (fx == 0 gives 0; the rare out-of-range case falls back to ldexp)
-__device__ inline double fx_to_double(long long fx, int s) {
-    if (fx == 0) return 0.0;
-    const double y = (double)fx;
-    const long long b = __double_as_longlong(y);
-    const int E = (int)((b >> 52) & 0x7FF);
-    if (E + s >= 1 && E + s <= 2046) return __longlong_as_double(b + ((long long)s << 52));
-    return ldexp(y, s);
-}
-
 // Persistent (one CTA per SM), warp-specialised: warp 0 issues the MMAs, warp 1 streams digit
 // stages with bulk copies (4-stage ring), warps 2..17 drain the TMEM accumulators (warp w reads
 // TMEM lanes 32 (w % 4) .. +31, columns 16 ((w - 2) / 4) .. +15).  The accumulators are released
-// as soon as they are folded into 64-bit fixed point in registers, so the next task's MMAs run
-// while the epilogue converts and updates C in FP64; the drain is on the critical path between
-// tasks, hence 16 epilogue warps.  N = 64 per task because TMEM holds the 7 groups x 64 columns.
+// once they are in registers (the FP64-accurate kernel: after the last TMEM load; the mixed
+// kernel: after the fold into 64-bit fixed point), so the next task's MMAs run while the epilogue
+// converts and updates C; the drain is on the critical path between tasks, hence 16 epilogue
+// warps.  N = 64 per task because TMEM holds the 7 groups x 64 columns.  Per task, the epilogue's
+// own work (fold, int64-to-FP64 conversion with integer instructions, one FP64 subtraction per
+// output, 64 KB of C read and written) is about as long as the MMAs.
 constexpr int OZ_EPI_WARPS = 16;                        // 4 per TMEM lane quarter
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_EPI_COLS = OZ_N * 4 / OZ_EPI_WARPS;   // accumulator columns per epilogue warp
@@ -484,6 +477,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                     }
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!MIXED && cb + 8 == OZ_EPI_COLS) {
+                    // the last accumulator columns are in registers: hand TMEM back to the MMA
+                    // warp before folding them, so the fold leaves the MMAs' critical path (the
+                    // mixed kernel, short of registers for it, releases after the fold)
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     // exact group sums -> fixed point with unit 2^-46 of s_r s_c.  Group g (at
@@ -505,10 +506,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                     fx[cb + j] = (long long)p01 * (1ll << 24) + (long long)p23 * (1ll << 8) + (iv4 + r56);
                 }
             }
-            // accumulators are in registers: hand TMEM back to the MMA warp
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+            if (MIXED) {
+                // accumulators are in registers: hand TMEM back to the MMA warp
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+            }
             const int* __restrict__ exp_a = (const int*)(sa + OZ_TILE_BYTES);
             const int* __restrict__ exp_b = (const int*)(sb + OZ_TILE_BYTES);
             // |mult| is a power of two: its exponent is read from the bits (ilogb costs a dozen
@@ -529,7 +532,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzJobList jobs, lo
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const double y = fx_to_double(negm ? -fx[h + j] : fx[h + j], er + eb[j]);
+                    // converted with integer instructions: the FP64 pipe, two lanes per clock
+                    // per SM, is left the subtraction alone
+                    const double y = fx_to_double_int(fx[h + j], er + eb[j], negm);
                     Cr[(long long)(h + j) * 128] = cv[j] - y;
                 }
             }
