@@ -745,12 +745,16 @@ def run_sim(args):
 
 
 def run_single_eval(args):
-    """One Algorithm 3 evaluation at theta^(0) on the FP64-accurate path (generation, Cholesky,
-    transforms), nothing else: the target of kernel captures on a small case."""
+    """One Algorithm 3 evaluation at theta^(0) (generation, Cholesky, transforms), nothing else:
+    the target of kernel captures on a small case.  FP64-accurate unless --precision mixed, which
+    runs the mixed path at --mixed-tol."""
     import torch
     import paper_2601_11437_gb300 as fbt
     w, locs, z = load_field(args.workload)
-    ctx = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_FP64_EMULATED)
+    if args.precision == "mixed":
+        ctx = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_MIXED, mixed_tol=args.mixed_tol)
+    else:
+        ctx = fbt.fbt_create(locs, z, nb=128, precision=fbt.PREC_FP64_EMULATED)
     ll, g, I = fbt.mle_eval(ctx, w.theta0)
     torch.cuda.synchronize()
     fbt.fbt_destroy(ctx)
@@ -783,7 +787,8 @@ def main():
                     help="batched workload: tune the FP64-accurate configuration per size band and the thread count")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint gradient on --workload")
     ap.add_argument("--single-eval", action="store_true",
-                    help="one FP64-accurate Algorithm 3 evaluation on --workload (a kernel-capture target)")
+                    help="one Algorithm 3 evaluation on --workload (a kernel-capture target; FP64-accurate "
+                         "unless --precision mixed)")
     ap.add_argument("--compare-mixed", action="store_true",
                     help="mixed against emulated FP64 on --workload (errors, Cholesky rate, estimates)")
     args = ap.parse_args()
