@@ -51,10 +51,10 @@ PRECISIONS = {"fp64": 0, "fp64_emulated": 1, "mixed": 2}
 # tensor-core work of one emulated FP64 tile product: 28 BF16 digit products of the same shape
 OZAKI_PRODUCTS = 28
 # DRAM bytes per 128 x 64 task of the emulated-FP64 tile update, from the ncu capture of one
-# launch of the two-sided transform's trailing update at n = 4096 (153.246 MB read + 71.072 MB
+# launch of the two-sided transform's trailing update at n = 4096 (156.671 MB read + 72.038 MB
 # written over the launch's 1984 tasks); the C tiles, which dominate it, grow in proportion to
 # the tasks
-OZAKI_DRAM_BYTES_PER_TASK = (153.246208e6 + 71.072e6) / 1984
+OZAKI_DRAM_BYTES_PER_TASK = (156.67072e6 + 72.0384e6) / 1984
 OZAKI_TASK_FLOPS = 2.0 * 128 * 64 * 128
 # FP64 peak for the roofline: the DFMA pipe, 2 FP64 FMA per clock per SM (measured on GB300:
 # 1.19 TFLOP/s sustained at ~1.99 GHz), 152 SMs, 2 flop per FMA, 2.07 GHz maximum SM clock.
