@@ -116,10 +116,11 @@ __device__ inline void cos24(int m, double& h, double& l) {
     l = neg ? -c_cos24[m][1] : c_cos24[m][1];
 }
 
-// one warp per interval
-__global__ void __launch_bounds__(256) k_interp_build(const ThetaConsts* __restrict__ tcp, QuadTables* __restrict__ qt) {
-    __shared__ double s_g[8][3][IP_DEG];
-    __shared__ double s_ch[8][3][IP_DEG], s_cl[8][3][IP_DEG];
+// one warp (one block) per interval: each lane's quadrature is a long FP64 chain, so the
+// intervals are spread over as many SMs as there are intervals
+__global__ void __launch_bounds__(32) k_interp_build(const ThetaConsts* __restrict__ tcp, QuadTables* __restrict__ qt) {
+    __shared__ double s_g[1][3][IP_DEG];
+    __shared__ double s_ch[1][3][IP_DEG], s_cl[1][3][IP_DEG];
     __shared__ int s_B[IP_DEG][IP_DEG];       // coefficient of t^i in T_k: s_B[k][i]
     if (threadIdx.x == 0) {
         for (int k = 0; k < IP_DEG; ++k)
@@ -130,8 +131,8 @@ __global__ void __launch_bounds__(256) k_interp_build(const ThetaConsts* __restr
             for (int i = 0; i < IP_DEG; ++i) s_B[k][i] = (i > 0 ? 2 * s_B[k - 1][i - 1] : 0) - s_B[k - 2][i];
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int iv = blockIdx.x * 8 + w;
+    const int w = 0, lane = threadIdx.x & 31;
+    const int iv = blockIdx.x;
     if (iv >= IP_INTERVALS) return;
     const int s = iv / IP_SUB, k = iv % IP_SUB;
     const double a = ldexp(1.0 + k / (double)IP_SUB, s), H = ldexp(1.0 / IP_SUB, s);
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(256) k_interp_build(const ThetaConsts* __restr
 
 static int launch_interp_build(Launcher& L, const ThetaConsts* tc, QuadTables* qt) {
     L.begin("prep_theta");
-    k_interp_build<<<(IP_INTERVALS + 7) / 8, 256, 0, L.stream>>>(tc, qt);
+    k_interp_build<<<IP_INTERVALS, 32, 0, L.stream>>>(tc, qt);
     L.count();
     return L.end(0.0, 0.0);
 }
