@@ -205,10 +205,10 @@ __device__ inline void tmem_ld8x(uint32_t taddr, uint32_t r[8]) {
 // once they are in registers (the FP64-accurate kernel: after the last TMEM load; the mixed
 // kernel: after the fold into 64-bit fixed point), so the next task's MMAs run while the epilogue
 // converts and updates C; the drain is on the critical path between tasks, hence 16 epilogue
-// warps.  N = 64 per task because TMEM holds the 7 groups x 64 columns.  Per task, the epilogue's
-// own work (drain and fold, int64-to-FP64 conversion with integer instructions, one FP64
-// subtraction per output, 64 KB of C read and written) takes longer than the MMAs and so sets
-// the task period.
+// warps.  N = 64 per task because TMEM holds the 7 groups x 64 columns.  The task period is the
+// MMAs (fed by a 42 KB operand stage per K = 16 from L2) plus the drain up to the hand-back of
+// TMEM; the rest of the epilogue (fold, int64-to-FP64 conversion with integer instructions, one
+// FP64 subtraction per output, 64 KB of C read and written) fits inside the next task's MMAs.
 constexpr int OZ_EPI_WARPS = 16;                        // 4 per TMEM lane quarter
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
 constexpr int OZ_EPI_COLS = OZ_N * 4 / OZ_EPI_WARPS;   // accumulator columns per epilogue warp
