@@ -771,7 +771,7 @@ def main():
     ap.add_argument("--workload", default="n65536")
     ap.add_argument("--nb", type=int, default=128)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64_emulated")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-sizes", type=lambda v: [int(x) for x in v.split(",")],
